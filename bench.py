@@ -1,0 +1,358 @@
+"""Benchmark of the leapfrog lattice-field hot path on GB300.
+
+Workload (one GPU, or N independent replicas under torchrun): a 256^3 complex (two real
+components) phi^4 field, V = lambda/4 (|phi|^2 - eta^2)^2 with lambda = eta = 1, dx = 1,
+dt = 0.05, phi0 components i.i.d. N(0, 0.1^2) (seeded), pi0 = 0.  A "step" is one leapfrog
+step of the whole lattice: force (7-point Laplacian + potential), kick and drift.
+
+The headline line times the FP64 path with the plain one-step-per-pass kernel (no temporal
+blocking).  The same line carries the FP32 path with the Kahan-compensated drift on the same
+lattice and initial data: its throughput, roofline fraction, speedup over FP64 and its error
+against the FP64 run.  The lattice state (805 MB FP64, 402 MB FP32+Kahan) is larger than the
+129 MB L2, so no flush is needed between steps.
+
+Metric: GSite-updates/s = sites x steps / seconds, with inputs resident in HBM.  The roofline
+counts compulsory HBM bytes per site-update: FP64 complex 64 B (read phi, read+write pi, write
+phi'), FP32+Kahan complex 48 B (plus read+write of the compensation).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (a bounded slab of the
+same lattice per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GSite-updates/s per leapfrog step and % of HBM roofline, FP32 vs FP64 at stated error"
+UNIT = "GSite-updates/s"
+N = 256
+NCOMP = 2
+KW = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+WORKLOAD = "phi4 complex 256^3 periodic lattice, dt=0.05, lambda=eta=1, sigma=0.1 Gaussian init"
+BYTES_PER_SITE = {"f64": 8 * NCOMP * 4, "f32k": 4 * NCOMP * 6, "f32": 4 * NCOMP * 4}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if key in d:
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        if shutil.which("nvidia-smi"):
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.tmp:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------- GPU arm helpers
+class WrappedPair:
+    """phi and pi as torch device tensors, borrowed by the library through lf2_field_wrap."""
+
+    def __init__(self, torch, lf2, prec, phi0):
+        self.torch, self.lf2, self.prec = torch, lf2, lf2.PRECISIONS[prec]
+        dtype = torch.float64 if prec == "f64" else torch.float32
+        self.phi = phi0.to(dtype).contiguous()
+        self.back = torch.empty_like(self.phi)
+        self.pi = torch.zeros_like(self.phi)
+        ptrs = [self.phi.data_ptr(), self.back.data_ptr()]
+        if self.prec == lf2.LF2_F32_KAHAN:
+            self.comp = torch.zeros_like(self.phi)
+            ptrs.append(self.comp.data_ptr())
+        self.lat = lf2.lf2_lattice_create((N, N, N))
+        self.fphi = lf2.lf2_field_wrap(self.lat, NCOMP, self.prec, ptrs)
+        self.fpi = lf2.lf2_field_wrap(self.lat, NCOMP, self.prec, [self.pi.data_ptr()])
+
+    def front(self):
+        ptr = self.lf2.lf2_field_buffer(self.fphi, 0)
+        return self.phi if ptr == self.phi.data_ptr() else self.back
+
+    def close(self):
+        self.lf2.lf2_field_free(self.fphi)
+        self.lf2.lf2_field_free(self.fpi)
+        self.lf2.lf2_lattice_destroy(self.lat)
+
+
+def time_steps(torch, lf2, pair, p, steps, warmup, stream):
+    """Warm-up, then EXACTLY `steps` leapfrog steps between CUDA events on the launch stream."""
+    lf2.lf2_leapfrog_init(pair.fphi, pair.fpi, p, stream)
+    for _ in range(warmup):
+        lf2.lf2_leapfrog(pair.fphi, pair.fpi, p, 1, stream)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        lf2.lf2_leapfrog(pair.fphi, pair.fpi, p, 1, stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(stop) / 1e3
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1508_05610_gb300 import build, inputs, lf2
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    lf2.load()
+    stream = torch.cuda.current_stream()
+    sites = N ** 3
+    p = lf2.params(**KW)
+    hbm_peak, peak_src = peaks()
+
+    phi0 = inputs.gaussian_field_device(N, N, N, NCOMP, sigma=0.1, seed=inputs.BASE_SEED + rank)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(t):
+        if dist is None:
+            return t
+        x = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        return float(x.item())
+
+    results = {}
+    with ClockSampler(local) as clocks:
+        for prec in ("f64", "f32k"):
+            pair = WrappedPair(torch, lf2, prec, phi0)
+            barrier()
+            t = max_over_ranks(time_steps(torch, lf2, pair, p, args.steps, args.warmup, stream))
+            results[prec] = t
+            pair.close()
+            del pair
+            torch.cuda.empty_cache()
+    clk = clocks.summary()
+
+    # error of the FP32+Kahan path against FP64 after 10 and 100 steps from the same data
+    err = {}
+    pairs = {prec: WrappedPair(torch, lf2, prec, phi0) for prec in ("f64", "f32k")}
+    done = 0
+    for prec in pairs:
+        lf2.lf2_leapfrog_init(pairs[prec].fphi, pairs[prec].fpi, p, stream)
+    for n in (10, 100):
+        for prec in pairs:
+            lf2.lf2_leapfrog(pairs[prec].fphi, pairs[prec].fpi, p, n - done, stream)
+        done = n
+        e64 = lf2.lf2_energy(pairs["f64"].fphi, pairs["f64"].fpi, p, stream)
+        e32 = lf2.lf2_energy(pairs["f32k"].fphi, pairs["f32k"].fpi, p, stream)
+        a, b = pairs["f32k"].front().double(), pairs["f64"].front()
+        pa, pb = pairs["f32k"].pi.double(), pairs["f64"].pi
+        err[str(n)] = {"phi_relmax": float((a - b).abs().max() / b.abs().max()),
+                       "pi_relmax": float((pa - pb).abs().max() / pb.abs().max()),
+                       "energy_rel": abs(e32["total"] - e64["total"]) / abs(e64["total"])}
+        del a, pa
+    for pair in pairs.values():
+        pair.close()
+    del pairs
+    torch.cuda.empty_cache()
+
+    # end to end through the public C API with host buffers: upload from pinned host memory,
+    # init, K steps, energy read-back, download of phi and pi.
+    host_phi = torch.empty((N, N, N, NCOMP), dtype=torch.float64, pin_memory=True)
+    host_phi.copy_(phi0)
+    host_pi = torch.zeros_like(host_phi).pin_memory()
+    out_phi = torch.empty_like(host_phi).pin_memory()
+    out_pi = torch.empty_like(host_phi).pin_memory()
+    import ctypes
+    dptr = ctypes.POINTER(ctypes.c_double)
+    with lf2.System((N, N, N), NCOMP, "f64") as s:
+        lib = lf2.load()
+        def e2e_once(nsteps):
+            lib.lf2_field_upload(s.phi, ctypes.cast(host_phi.data_ptr(), dptr), stream.cuda_stream)
+            lib.lf2_field_upload(s.pi, ctypes.cast(host_pi.data_ptr(), dptr), stream.cuda_stream)
+            lf2.lf2_leapfrog_init(s.phi, s.pi, p, stream)
+            lf2.lf2_leapfrog(s.phi, s.pi, p, nsteps, stream)
+            lf2.lf2_energy(s.phi, s.pi, p, stream)
+            lib.lf2_field_download(s.phi, ctypes.cast(out_phi.data_ptr(), dptr), stream.cuda_stream)
+            lib.lf2_field_download(s.pi, ctypes.cast(out_pi.data_ptr(), dptr), stream.cuda_stream)
+        e2e_once(args.warmup)
+        barrier()
+        t0 = time.perf_counter()
+        e2e_once(args.steps)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+    state_bytes = N ** 3 * NCOMP * 8 * 2
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    def gsu(t):
+        return sites * world * args.steps / t / 1e9
+
+    def roof(prec, t):
+        per_launch = t / args.steps
+        achieved = BYTES_PER_SITE[prec] * sites / per_launch / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "peak_source": f"{peak_src} HBM copy bandwidth",
+                "bytes_per_site_update": BYTES_PER_SITE[prec]}
+
+    t64, t32 = results["f64"], results["f32k"]
+    line = {
+        "metric": METRIC, "value": round(gsu(t64), 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t64 / args.steps * 1e3, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian phi0)",
+        "config": {"workload": WORKLOAD + ", FP64, one step per HBM pass (plain path)", "lattice": [N, N, N],
+                   "ncomp": NCOMP, "sites": sites, "precision": "f64", "parallelism": f"replicas x{world}",
+                   "l2_policy": "state 805 MB > 129 MB L2; no flush needed"},
+        "roofline": roof("f64", t64),
+        "fp32_kahan": {"value": round(gsu(t32), 3), "unit": UNIT, "ms_per_step": round(t32 / args.steps * 1e3, 5),
+                       "roofline": roof("f32k", t32), "speedup_vs_fp64": round(t64 / t32, 3),
+                       "error_vs_fp64": err},
+        "e2e": {"value": round(sites * world * args.steps / t_e2e / 1e9, 3), "unit": UNIT,
+                "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": (state_bytes + 64) / args.steps,
+                "note": "upload phi,pi from pinned host + half-kick + K steps + energy + download, per step"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU baseline arm
+def oracle_rate(nz_slab, steps, threads):
+    """FP64 CPU oracle on a 256 x 256 x nz_slab periodic slab of the workload."""
+    from oracle import oracle
+    from paper_1508_05610_gb300 import inputs
+    phi0 = inputs.gaussian_field(N, N, nz_slab, NCOMP, sigma=0.1, seed=inputs.BASE_SEED)
+    pi0 = phi0 * 0.0
+    phi, pi = oracle.evolve(phi0, pi0, 0, half_kick=True, threads=threads, **KW)
+    t0 = time.perf_counter()
+    oracle.evolve(phi, pi, steps, threads=threads, **KW)
+    dt = time.perf_counter() - t0
+    return N * N * nz_slab * steps / dt / 1e9, dt
+
+
+def cpu_baseline():
+    threads = os.cpu_count() or 1
+    nz_slab, steps = 64, 20
+    v, dt = oracle_rate(nz_slab, steps, threads)
+    return {"value": round(v, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle, {steps} steps of a 256x256x{nz_slab} complex slab of the workload "
+                      f"(OpenMP over z-planes), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    nz_slab = 16
+    from oracle import oracle
+    from paper_1508_05610_gb300 import inputs
+    phi0 = inputs.gaussian_field(N, N, nz_slab, NCOMP, sigma=0.1, seed=inputs.BASE_SEED)
+    phi, pi = oracle.evolve(phi0, phi0 * 0.0, 0, half_kick=True, threads=threads, **KW)
+    for _ in range(args.warmup):
+        phi, pi = oracle.evolve(phi, pi, 1, threads=threads, **KW)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        phi, pi = oracle.evolve(phi, pi, 1, threads=threads, **KW)
+    dt = time.perf_counter() - t0
+    sites = N * N * nz_slab
+    v = sites * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian phi0)",
+            "config": {"workload": WORKLOAD + ", FP64 CPU oracle", "lattice": [N, N, nz_slab], "ncomp": NCOMP},
+            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step: one leapfrog step of a 256x256x{nz_slab} periodic slab"},
+            "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lf2", choices=["lf2", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * lf2.h -- C ABI of liblf2, a GB300 (sm_103a) implementation of the leapfrog evolution of a
+ * classical scalar field on a periodic 3-D cartesian lattice, following the Lattice / Field /
+ * Site / updateHalo model of LATfield2 (Daverio, Hindmarsh & Bevis, arXiv:1508.05610).
+ *
+ * The method (the paper describes the data model; the equation of motion is the standard one
+ * for the classical field simulations the library was written for, Sec. 1 and Sec. 5):
+ *
+ *   field      phi_a(x), a = 0 .. ncomp-1 (ncomp = 1: real, 2: complex as two reals)
+ *   potential  V = lambda/4 (sum_b phi_b^2 - eta^2)^2 + m2/2 sum_a phi_a^2
+ *   force      F_a(x) = (1/dx^2) sum_{i=0..2} [phi_a(x+i) + phi_a(x-i) - 2 phi_a(x)]
+ *                       - lambda phi_a (sum_b phi_b^2 - eta^2) - m2 phi_a
+ *              (the 7-point Laplacian built from the Site neighbours x+i, x-i, Sec. 3.4)
+ *   leapfrog   pi_{n+1/2} = pi_{n-1/2} + dt F(phi_n);   phi_{n+1} = phi_n + dt pi_{n+1/2}
+ *              (staggered: pi lives at half steps; one force evaluation per step)
+ *   start      pi_{-1/2} = pi_0 - (dt/2) F(phi_0)
+ *
+ * Boundary conditions are periodic, the only ones LATfield2 has (Sec. 3.2, Sec. 3.3.1): the
+ * lattice is a torus.  LATfield2 stores a halo of h sites around the local block and fills it
+ * with updateHalo(); on one GPU the same periodic images are read in-kernel by wrapped
+ * indexing, so no halo is stored and lf2_field_update_halo() only validates its argument.
+ *
+ * Memory layout of every field buffer (device and host): row-major with x (dimension 0)
+ * fastest, then y, then z, and the ncomp components of a site next to each other -- the
+ * Site order and the per-site component lists of the paper's binary files (Sec. 3.4, 3.5).
+ * Element (x, y, z, a) is at offset ((z * Ny + y) * Nx + x) * ncomp + a.
+ *
+ * Precisions:
+ *   LF2_F64        phi, pi in double; all arithmetic in double.
+ *   LF2_F32_KAHAN  phi, pi in float; the drift phi += dt pi is Kahan-compensated with a
+ *                  per-site float compensation term owned by the phi field; energies and
+ *                  checksums are accumulated in double.
+ *   LF2_F32        phi, pi in float with an uncompensated drift (ablation).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an lf2_status; LF2_OK is 0.  No C++ exception crosses the ABI.
+ *   - On error the output handle is left untouched and lf2_last_error() returns a
+ *     human-readable message for the calling thread.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *     Calls enqueue work on the stream and return without waiting unless stated otherwise.
+ *   - Handles are opaque and owned by the caller, who frees them with the matching
+ *     destroy/free call.  Handles are not thread-safe; use one handle from one thread at a time.
+ *   - All device memory belongs to the current CUDA device at creation time.
+ */
+#ifndef LF2_H
+#define LF2_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LF2_OK = 0,
+    LF2_ERR_INVALID = 1,     /* bad argument: NULL pointer, size, mismatched fields ... */
+    LF2_ERR_UNSUPPORTED = 2, /* valid in the paper's model but not built: dim != 3, ncomp > 2 */
+    LF2_ERR_NOMEM = 3,       /* a device or host allocation failed */
+    LF2_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    LF2_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (ensemble runs) */
+    LF2_ERR_STATE = 6        /* call not allowed in the object's current state */
+} lf2_status;
+
+typedef enum { LF2_F64 = 0, LF2_F32_KAHAN = 1, LF2_F32 = 2 } lf2_precision;
+
+typedef struct lf2_lattice_s *lf2_lattice;
+typedef struct lf2_field_s *lf2_field;
+typedef struct lf2_ensemble_s *lf2_ensemble;
+
+/* Model and integrator parameters (double for every precision; converted once per call). */
+typedef struct {
+    double dx;     /* lattice spacing, > 0 */
+    double dt;     /* time step; may be negative (time reversal) */
+    double lambda; /* quartic coupling */
+    double eta;    /* vacuum expectation value */
+    double m2;     /* mass term m^2 (0 for the pure phi^4 potential) */
+} lf2_params;
+
+/* Energy and checksums at integer step n (see lf2_energy).  All values are FP64. */
+typedef struct {
+    double kinetic;   /* dx^3 sum_x 1/2 sum_a pi_{a,n}^2 */
+    double gradient;  /* dx^3 sum_x sum_a sum_i (phi_a(x+i) - phi_a(x))^2 / (2 dx^2) */
+    double potential; /* dx^3 sum_x V(phi(x)) */
+    double total;     /* kinetic + gradient + potential */
+    double sum[2];    /* sum_x phi_a(x) per component (unused entries 0) */
+    double sum_sq[2]; /* sum_x phi_a(x)^2 per component (unused entries 0) */
+} lf2_energy_t;
+
+/* Kernel selection for lf2_leapfrog_ex.  Every variant computes bitwise the same result. */
+typedef enum {
+    LF2_KERNEL_AUTO = 0,     /* tuned choice (the one lf2_leapfrog uses) */
+    LF2_KERNEL_SITE = 1,     /* one thread per site, any lattice shape */
+    LF2_KERNEL_STREAM = 2,   /* x-y tile streaming along z, one step per pass */
+    LF2_KERNEL_TBLOCK = 3    /* temporal blocking: `depth` steps per pass */
+} lf2_kernel;
+
+typedef struct {
+    int kernel; /* lf2_kernel */
+    int tile_y; /* rows of the x-y tile (STREAM, TBLOCK); 0 = default */
+    int zchunk; /* z-planes per block (STREAM, TBLOCK); 0 = default */
+    int depth;  /* temporal-blocking depth, steps fused per pass (TBLOCK); 0 = default */
+} lf2_step_config;
+
+/* ---------------------------------------------------------------------- lattice */
+
+/* Lattice(dim, sizes, h) of Sec. 3.2: a dim-dimensional periodic cartesian lattice with
+ * sizes[0..dim) sites per dimension (sizes[0] is x, the fastest) and a halo of `halo` sites.
+ * Returns LF2_ERR_UNSUPPORTED for dim != 3 (the paper allows dim >= 2; this build is 3-D),
+ * LF2_ERR_INVALID for halo < 1, any size < 1, or more than 2^40 sites.  The halo width is
+ * recorded for fidelity with the paper's model; the 7-point stencil needs 1. */
+lf2_status lf2_lattice_create(int dim, const int *sizes, int halo, lf2_lattice *out);
+
+/* Frees the lattice.  LF2_ERR_STATE while any field or ensemble still uses it. */
+lf2_status lf2_lattice_destroy(lf2_lattice lat);
+
+/* Number of sites Nx*Ny*Nz. */
+lf2_status lf2_lattice_sites(lf2_lattice lat, long long *out);
+
+/* ------------------------------------------------------------------------ field */
+
+/* Field<T>(lat, comp) of Sec. 3.3: allocates one device buffer of sites*ncomp elements of
+ * the precision's storage type, zero-filled.  ncomp must be 1 or 2 (LF2_ERR_UNSUPPORTED
+ * otherwise).  A field used as phi by lf2_leapfrog also gets a back buffer and, for
+ * LF2_F32_KAHAN, a zeroed float compensation buffer; they are allocated by
+ * lf2_leapfrog_init or, failing that, by the first lf2_leapfrog on the field -- before any
+ * stream capture.  The library owns these buffers. */
+lf2_status lf2_field_alloc(lf2_lattice lat, int ncomp, lf2_precision prec, lf2_field *out);
+
+/* Like lf2_field_alloc, but the buffers are borrowed from the caller (for example torch
+ * tensors), who must keep them alive and contiguous until lf2_field_free.  dev_ptrs[0] is
+ * the value buffer; dev_ptrs[1] (optional) the phi back buffer; dev_ptrs[2] (optional,
+ * LF2_F32_KAHAN only) the float compensation buffer.  nptrs is 1, 2 or 3.  Every pointer
+ * must be 16-byte aligned.  Buffers not given are allocated by the library when needed. */
+lf2_status lf2_field_wrap(lf2_lattice lat, int ncomp, lf2_precision prec, void *const *dev_ptrs,
+                          int nptrs, lf2_field *out);
+
+/* Frees the field and every buffer the library allocated for it. */
+lf2_status lf2_field_free(lf2_field f);
+
+/* Device address of one of the field's buffers: which = 0 the current value buffer (it
+ * changes after each lf2_leapfrog step, because phi's front and back buffers swap), 1 the
+ * back buffer, 2 the compensation buffer.  *out is NULL if that buffer does not exist. */
+lf2_status lf2_field_buffer(lf2_field f, int which, void **out);
+
+/* Copies sites*ncomp doubles from host memory (the layout above) into the field, converting
+ * to the storage precision on the device; for LF2_F32_KAHAN the compensation is reset to 0.
+ * Returns after the host buffer may be reused (the call synchronises `stream`). */
+lf2_status lf2_field_upload(lf2_field f, const double *host, void *stream);
+
+/* Copies the field's current values to sites*ncomp host doubles; synchronises `stream`. */
+lf2_status lf2_field_download(lf2_field f, double *host, void *stream);
+
+/* updateHalo() of Sec. 3.3.1.  The GPU kernels read periodic images by wrapped indexing,
+ * so there is no stored halo to refresh: this validates the handle and returns LF2_OK. */
+lf2_status lf2_field_update_halo(lf2_field f, void *stream);
+
+/* -------------------------------------------------------------------- leapfrog */
+
+/* Start of the staggered leapfrog: pi <- pi - (dt/2) F(phi), turning pi_0 into pi_{-1/2}.
+ * phi and pi must share the lattice, ncomp and precision.  Also allocates phi's back and
+ * compensation buffers if missing (so that later lf2_leapfrog calls allocate nothing). */
+lf2_status lf2_leapfrog_init(lf2_field phi, lf2_field pi, const lf2_params *p, void *stream);
+
+/* nsteps >= 0 leapfrog steps.  On entry phi holds phi_n and pi holds pi_{n-1/2}; on return
+ * phi holds phi_{n+nsteps} and pi holds pi_{n+nsteps-1/2}.  phi's front and back buffers swap
+ * after each step (no copy).  Uses the tuned kernel of lf2_tune when one was chosen for this
+ * shape, else the default one; results are bitwise identical whichever kernel runs. */
+lf2_status lf2_leapfrog(lf2_field phi, lf2_field pi, const lf2_params *p, int nsteps, void *stream);
+
+/* lf2_leapfrog with an explicit kernel choice (testing and tuning).  LF2_ERR_UNSUPPORTED if the
+ * chosen kernel cannot run this lattice (for example x rows not a multiple of 16 bytes). */
+lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int nsteps,
+                           const lf2_step_config *cfg, void *stream);
+
+/* Energy and checksums at integer step n from phi_n and pi_{n-1/2}: the synchronised momentum
+ * pi_n = pi_{n-1/2} + (dt/2) F(phi_n) is formed on the fly.  Accumulates in FP64 for every
+ * precision, with a fixed reduction order (bitwise reproducible).  Writes *out and
+ * synchronises `stream`. */
+lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream);
+
+/* ------------------------------------------------------------------- utilities */
+
+const char *lf2_status_string(lf2_status s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lf2_last_error(void);
+
+/* Library version string. */
+const char *lf2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LF2_H */

@@ -1,0 +1,436 @@
+// lf2_api.cu -- the C ABI of liblf2: handles, argument checks, status mapping, dispatch.
+//
+// Lattice and Field follow LATfield2's model (arXiv:1508.05610): Lattice(dim, sizes, h) of
+// Sec. 3.2 and Field<T>(lat, comp) of Sec. 3.3, with updateHalo() of Sec. 3.3.1 reduced to a
+// check because the kernels read periodic images by wrapped indexing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lf2_internal.cuh"
+
+using namespace lf2;
+
+struct lf2_lattice_s {
+    int dim;
+    int n[3];
+    int halo;
+    long long sites;
+    std::atomic<int> users{0};  // fields and ensembles still attached
+};
+
+struct lf2_field_s {
+    lf2_lattice lat = nullptr;
+    int ncomp = 0;
+    lf2_precision prec = LF2_F64;
+    size_t esize = 0;  // bytes per stored element
+    long long count = 0;  // sites * ncomp
+    void *val[2] = {nullptr, nullptr};
+    bool own_val[2] = {false, false};
+    int front = 0;
+    float *comp = nullptr;
+    bool own_comp = false;
+    double *energy_scratch = nullptr;  // kEnergyBlocks*8 partials + 8 results (device)
+    double *energy_host = nullptr;     // 8 pinned doubles
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lf2_status fail(lf2_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+lf2_status fail(lf2_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+lf2_status cuda_fail(cudaError_t e, const char *what) {
+    const lf2_status s = (e == cudaErrorMemoryAllocation) ? LF2_ERR_NOMEM : LF2_ERR_CUDA;
+    return fail(s, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define LF2_CUDA(call, what)                                   \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return cuda_fail(_e, (what));   \
+    } while (0)
+
+size_t elem_size(lf2_precision p) { return p == LF2_F64 ? sizeof(double) : sizeof(float); }
+
+bool valid_prec(int p) { return p == LF2_F64 || p == LF2_F32_KAHAN || p == LF2_F32; }
+
+Geom geom_of(const lf2_lattice_s *lat) { return Geom{lat->n[0], lat->n[1], lat->n[2], lat->sites}; }
+
+lf2_status check_params(const lf2_params *p) {
+    if (!p) return fail(LF2_ERR_INVALID, "params is NULL");
+    if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return fail(LF2_ERR_INVALID, "dx must be finite and > 0");
+    if (!std::isfinite(p->dt) || !std::isfinite(p->lambda) || !std::isfinite(p->eta) || !std::isfinite(p->m2))
+        return fail(LF2_ERR_INVALID, "non-finite parameter");
+    return LF2_OK;
+}
+
+lf2_status check_pair(lf2_field phi, lf2_field pi) {
+    if (!phi || !pi) return fail(LF2_ERR_INVALID, "field handle is NULL");
+    if (phi == pi) return fail(LF2_ERR_INVALID, "phi and pi must be different fields");
+    if (phi->lat != pi->lat) return fail(LF2_ERR_INVALID, "phi and pi live on different lattices");
+    if (phi->ncomp != pi->ncomp) return fail(LF2_ERR_INVALID, "phi and pi have different ncomp");
+    if (phi->prec != pi->prec) return fail(LF2_ERR_INVALID, "phi and pi have different precision");
+    return LF2_OK;
+}
+
+// Back buffer and compensation of a field used as phi.
+lf2_status ensure_dynamic(lf2_field phi, cudaStream_t s) {
+    const size_t bytes = (size_t)phi->count * phi->esize;
+    if (!phi->val[1 - phi->front]) {
+        void *b = nullptr;
+        if (getenv("LF2_FAULT") && !strcmp(getenv("LF2_FAULT"), "alloc"))
+            return fail(LF2_ERR_NOMEM, "allocation failure injected by LF2_FAULT=alloc");
+        LF2_CUDA(cudaMalloc(&b, bytes ? bytes : 16), "cudaMalloc(phi back buffer)");
+        phi->val[1 - phi->front] = b;
+        phi->own_val[1 - phi->front] = true;
+    }
+    if (phi->prec == LF2_F32_KAHAN && !phi->comp) {
+        void *c = nullptr;
+        const size_t cb = (size_t)phi->count * sizeof(float);
+        LF2_CUDA(cudaMalloc(&c, cb ? cb : 16), "cudaMalloc(compensation)");
+        phi->comp = (float *)c;
+        phi->own_comp = true;
+        LF2_CUDA(cudaMemsetAsync(c, 0, cb, s), "cudaMemsetAsync(compensation)");
+    }
+    return LF2_OK;
+}
+
+lf2_status ensure_energy_scratch(lf2_field f) {
+    if (!f->energy_scratch) {
+        void *d = nullptr;
+        LF2_CUDA(cudaMalloc(&d, sizeof(double) * (kEnergyBlocks * 8 + 8)), "cudaMalloc(energy scratch)");
+        f->energy_scratch = (double *)d;
+    }
+    if (!f->energy_host) {
+        void *h = nullptr;
+        LF2_CUDA(cudaMallocHost(&h, sizeof(double) * 8), "cudaMallocHost(energy result)");
+        f->energy_host = (double *)h;
+    }
+    return LF2_OK;
+}
+
+StepArgs step_args(lf2_field phi, lf2_field pi, const lf2_params *p, double dt, bool drift) {
+    StepArgs a;
+    a.phi = phi->val[phi->front];
+    a.phi_out = phi->val[1 - phi->front];
+    a.pi = pi->val[0];
+    a.comp = phi->comp;
+    a.g = geom_of(phi->lat);
+    a.ncomp = phi->ncomp;
+    a.prec = phi->prec;
+    a.p = *p;
+    a.dt = dt;
+    a.drift = drift;
+    return a;
+}
+
+lf2_status new_field(lf2_lattice lat, int ncomp, int prec, lf2_field *out) {
+    if (!lat || !out) return fail(LF2_ERR_INVALID, "lattice or output pointer is NULL");
+    if (!valid_prec(prec)) return fail(LF2_ERR_INVALID, "unknown precision %d", prec);
+    if (ncomp < 1) return fail(LF2_ERR_INVALID, "ncomp must be >= 1");
+    if (ncomp > kMaxComp) return fail(LF2_ERR_UNSUPPORTED, "ncomp %d not built (1 or 2)", ncomp);
+    return LF2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lf2_status_string(lf2_status s) {
+    switch (s) {
+        case LF2_OK: return "LF2_OK";
+        case LF2_ERR_INVALID: return "LF2_ERR_INVALID";
+        case LF2_ERR_UNSUPPORTED: return "LF2_ERR_UNSUPPORTED";
+        case LF2_ERR_NOMEM: return "LF2_ERR_NOMEM";
+        case LF2_ERR_CUDA: return "LF2_ERR_CUDA";
+        case LF2_ERR_TIMEOUT: return "LF2_ERR_TIMEOUT";
+        case LF2_ERR_STATE: return "LF2_ERR_STATE";
+    }
+    return "LF2_ERR_UNKNOWN";
+}
+
+const char *lf2_last_error(void) { return g_last_error.c_str(); }
+
+const char *lf2_version(void) { return "lf2 0.1 (sm_103a)"; }
+
+lf2_status lf2_lattice_create(int dim, const int *sizes, int halo, lf2_lattice *out) {
+    if (!sizes || !out) return fail(LF2_ERR_INVALID, "sizes or output pointer is NULL");
+    if (dim < 2) return fail(LF2_ERR_INVALID, "dim must be >= 2 (got %d)", dim);
+    if (dim != 3) return fail(LF2_ERR_UNSUPPORTED, "only 3-D lattices are built (got dim=%d)", dim);
+    if (halo < 1) return fail(LF2_ERR_INVALID, "halo must be >= 1 (got %d)", halo);
+    long long sites = 1;
+    for (int i = 0; i < 3; ++i) {
+        if (sizes[i] < 1) return fail(LF2_ERR_INVALID, "sizes[%d] = %d must be >= 1", i, sizes[i]);
+        sites *= sizes[i];
+        if (sites > (1LL << 40)) return fail(LF2_ERR_INVALID, "lattice too large");
+    }
+    lf2_lattice_s *l = new (std::nothrow) lf2_lattice_s;
+    if (!l) return fail(LF2_ERR_NOMEM, "host allocation failed");
+    l->dim = dim;
+    for (int i = 0; i < 3; ++i) l->n[i] = sizes[i];
+    l->halo = halo;
+    l->sites = sites;
+    *out = l;
+    return LF2_OK;
+}
+
+lf2_status lf2_lattice_destroy(lf2_lattice lat) {
+    if (!lat) return fail(LF2_ERR_INVALID, "lattice is NULL");
+    if (lat->users.load() != 0) return fail(LF2_ERR_STATE, "lattice still used by %d field(s)", lat->users.load());
+    delete lat;
+    return LF2_OK;
+}
+
+lf2_status lf2_lattice_sites(lf2_lattice lat, long long *out) {
+    if (!lat || !out) return fail(LF2_ERR_INVALID, "NULL argument");
+    *out = lat->sites;
+    return LF2_OK;
+}
+
+lf2_status lf2_field_alloc(lf2_lattice lat, int ncomp, lf2_precision prec, lf2_field *out) {
+    lf2_status st = new_field(lat, ncomp, prec, out);
+    if (st != LF2_OK) return st;
+    lf2_field_s *f = new (std::nothrow) lf2_field_s;
+    if (!f) return fail(LF2_ERR_NOMEM, "host allocation failed");
+    f->lat = lat;
+    f->ncomp = ncomp;
+    f->prec = prec;
+    f->esize = elem_size(prec);
+    f->count = lat->sites * ncomp;
+    const size_t bytes = (size_t)f->count * f->esize;
+    if (getenv("LF2_FAULT") && !strcmp(getenv("LF2_FAULT"), "alloc")) {
+        delete f;
+        return fail(LF2_ERR_NOMEM, "allocation failure injected by LF2_FAULT=alloc");
+    }
+    cudaError_t e = cudaMalloc(&f->val[0], bytes);
+    if (e == cudaSuccess) e = cudaMemset(f->val[0], 0, bytes);
+    if (e != cudaSuccess) {
+        if (f->val[0]) cudaFree(f->val[0]);
+        delete f;
+        return cuda_fail(e, "cudaMalloc(field)");
+    }
+    f->own_val[0] = true;
+    lat->users++;
+    *out = f;
+    return LF2_OK;
+}
+
+lf2_status lf2_field_wrap(lf2_lattice lat, int ncomp, lf2_precision prec, void *const *dev_ptrs, int nptrs,
+                          lf2_field *out) {
+    lf2_status st = new_field(lat, ncomp, prec, out);
+    if (st != LF2_OK) return st;
+    if (!dev_ptrs || nptrs < 1 || nptrs > 3) return fail(LF2_ERR_INVALID, "nptrs must be 1, 2 or 3");
+    if (nptrs == 3 && prec != LF2_F32_KAHAN) return fail(LF2_ERR_INVALID, "a compensation buffer needs LF2_F32_KAHAN");
+    for (int i = 0; i < nptrs; ++i) {
+        if (!dev_ptrs[i]) return fail(LF2_ERR_INVALID, "dev_ptrs[%d] is NULL", i);
+        if ((uintptr_t)dev_ptrs[i] % 16) return fail(LF2_ERR_INVALID, "dev_ptrs[%d] is not 16-byte aligned", i);
+    }
+    lf2_field_s *f = new (std::nothrow) lf2_field_s;
+    if (!f) return fail(LF2_ERR_NOMEM, "host allocation failed");
+    f->lat = lat;
+    f->ncomp = ncomp;
+    f->prec = prec;
+    f->esize = elem_size(prec);
+    f->count = lat->sites * ncomp;
+    f->val[0] = dev_ptrs[0];
+    if (nptrs >= 2) f->val[1] = dev_ptrs[1];
+    if (nptrs >= 3) f->comp = (float *)dev_ptrs[2];
+    lat->users++;
+    *out = f;
+    return LF2_OK;
+}
+
+lf2_status lf2_field_free(lf2_field f) {
+    if (!f) return fail(LF2_ERR_INVALID, "field is NULL");
+    for (int i = 0; i < 2; ++i)
+        if (f->own_val[i] && f->val[i]) cudaFree(f->val[i]);
+    if (f->own_comp && f->comp) cudaFree(f->comp);
+    if (f->energy_scratch) cudaFree(f->energy_scratch);
+    if (f->energy_host) cudaFreeHost(f->energy_host);
+    f->lat->users--;
+    delete f;
+    return LF2_OK;
+}
+
+lf2_status lf2_field_buffer(lf2_field f, int which, void **out) {
+    if (!f || !out) return fail(LF2_ERR_INVALID, "NULL argument");
+    switch (which) {
+        case 0: *out = f->val[f->front]; break;
+        case 1: *out = f->val[1 - f->front]; break;
+        case 2: *out = f->comp; break;
+        default: return fail(LF2_ERR_INVALID, "which must be 0, 1 or 2");
+    }
+    return LF2_OK;
+}
+
+lf2_status lf2_field_upload(lf2_field f, const double *host, void *stream) {
+    if (!f || !host) return fail(LF2_ERR_INVALID, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t total = (size_t)f->count;
+    if (f->prec == LF2_F64) {
+        LF2_CUDA(cudaMemcpyAsync(f->val[f->front], host, total * sizeof(double), cudaMemcpyHostToDevice, s),
+                 "upload copy");
+    } else {
+        // Stage chunks of doubles on the device and convert there.
+        const size_t chunk = std::min(total, (size_t)1 << 24);
+        double *stage = nullptr;
+        if (chunk) LF2_CUDA(cudaMalloc(&stage, chunk * sizeof(double)), "cudaMalloc(upload staging)");
+        for (size_t off = 0; off < total; off += chunk) {
+            const size_t n = std::min(chunk, total - off);
+            cudaError_t e = cudaMemcpyAsync(stage, host + off, n * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = launch_convert_from_f64(stage, (float *)f->val[f->front] + off, (long long)n, f->prec, s);
+            if (e != cudaSuccess) {
+                cudaFree(stage);
+                return cuda_fail(e, "upload");
+            }
+        }
+        if (f->comp) {
+            cudaError_t e = cudaMemsetAsync(f->comp, 0, total * sizeof(float), s);
+            if (e != cudaSuccess) {
+                cudaFree(stage);
+                return cuda_fail(e, "reset compensation");
+            }
+        }
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (stage) cudaFree(stage);
+        if (e != cudaSuccess) return cuda_fail(e, "upload sync");
+        return LF2_OK;
+    }
+    if (f->comp) LF2_CUDA(cudaMemsetAsync(f->comp, 0, total * sizeof(float), s), "reset compensation");
+    LF2_CUDA(cudaStreamSynchronize(s), "upload sync");
+    return LF2_OK;
+}
+
+lf2_status lf2_field_download(lf2_field f, double *host, void *stream) {
+    if (!f || !host) return fail(LF2_ERR_INVALID, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t total = (size_t)f->count;
+    if (f->prec == LF2_F64) {
+        LF2_CUDA(cudaMemcpyAsync(host, f->val[f->front], total * sizeof(double), cudaMemcpyDeviceToHost, s),
+                 "download copy");
+        LF2_CUDA(cudaStreamSynchronize(s), "download sync");
+        return LF2_OK;
+    }
+    const size_t chunk = std::min(total, (size_t)1 << 24);
+    double *stage = nullptr;
+    if (chunk) LF2_CUDA(cudaMalloc(&stage, chunk * sizeof(double)), "cudaMalloc(download staging)");
+    for (size_t off = 0; off < total; off += chunk) {
+        const size_t n = std::min(chunk, total - off);
+        cudaError_t e = launch_convert_to_f64((const float *)f->val[f->front] + off, stage, (long long)n, f->prec, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host + off, stage, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(stage);
+            return cuda_fail(e, "download");
+        }
+    }
+    if (stage) cudaFree(stage);
+    return LF2_OK;
+}
+
+lf2_status lf2_field_update_halo(lf2_field f, void *stream) {
+    (void)stream;
+    if (!f) return fail(LF2_ERR_INVALID, "field is NULL");
+    return LF2_OK;
+}
+
+lf2_status lf2_leapfrog_init(lf2_field phi, lf2_field pi, const lf2_params *p, void *stream) {
+    lf2_status st = check_pair(phi, pi);
+    if (st == LF2_OK) st = check_params(p);
+    if (st != LF2_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = ensure_dynamic(phi, s);
+    if (st != LF2_OK) return st;
+    st = ensure_energy_scratch(phi);
+    if (st != LF2_OK) return st;
+    const StepArgs a = step_args(phi, pi, p, -0.5 * p->dt, false);
+    LF2_CUDA(launch_site_step(a, s), "half-kick launch");
+    return LF2_OK;
+}
+
+lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int nsteps, const lf2_step_config *cfg,
+                           void *stream) {
+    lf2_status st = check_pair(phi, pi);
+    if (st == LF2_OK) st = check_params(p);
+    if (st != LF2_OK) return st;
+    if (nsteps < 0) return fail(LF2_ERR_INVALID, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = ensure_dynamic(phi, s);
+    if (st != LF2_OK) return st;
+    int kernel = cfg ? cfg->kernel : LF2_KERNEL_AUTO;
+    const int tile_y = cfg ? cfg->tile_y : 0;
+    const int zchunk = cfg ? cfg->zchunk : 0;
+    if (kernel < LF2_KERNEL_AUTO || kernel > LF2_KERNEL_TBLOCK) return fail(LF2_ERR_INVALID, "unknown kernel %d", kernel);
+    {
+        const StepArgs probe = step_args(phi, pi, p, p->dt, true);
+        if (kernel == LF2_KERNEL_AUTO) kernel = stream_supported(probe, 0, 0) ? LF2_KERNEL_STREAM : LF2_KERNEL_SITE;
+        if (kernel == LF2_KERNEL_STREAM && !stream_supported(probe, tile_y, zchunk))
+            return fail(LF2_ERR_UNSUPPORTED, "streaming kernel does not fit this lattice/config");
+        if (kernel == LF2_KERNEL_TBLOCK) return fail(LF2_ERR_UNSUPPORTED, "temporal blocking not built yet");
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        const StepArgs a = step_args(phi, pi, p, p->dt, true);
+        cudaError_t e = (kernel == LF2_KERNEL_STREAM) ? launch_stream_step(a, tile_y, zchunk, nsteps, s)
+                                                      : launch_site_step(a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "leapfrog launch");
+        phi->front = 1 - phi->front;
+    }
+    return LF2_OK;
+}
+
+lf2_status lf2_leapfrog(lf2_field phi, lf2_field pi, const lf2_params *p, int nsteps, void *stream) {
+    return lf2_leapfrog_ex(phi, pi, p, nsteps, nullptr, stream);
+}
+
+lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream) {
+    lf2_status st = check_pair(phi, pi);
+    if (st == LF2_OK) st = check_params(p);
+    if (st != LF2_OK) return st;
+    if (!out) return fail(LF2_ERR_INVALID, "output pointer is NULL");
+    st = ensure_energy_scratch(phi);
+    if (st != LF2_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *partials = phi->energy_scratch;
+    double *result = phi->energy_scratch + kEnergyBlocks * 8;
+    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[0], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
+                           result, s),
+             "energy launch");
+    LF2_CUDA(cudaMemcpyAsync(phi->energy_host, result, 8 * sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
+    LF2_CUDA(cudaStreamSynchronize(s), "energy sync");
+    const double *r = phi->energy_host;
+    const double vol = p->dx * p->dx * p->dx;
+    lf2_energy_t e;
+    memset(&e, 0, sizeof e);
+    e.kinetic = vol * r[0];
+    e.gradient = vol * r[1];
+    e.potential = vol * r[2];
+    e.total = e.kinetic + e.gradient + e.potential;
+    for (int a = 0; a < phi->ncomp; ++a) {
+        e.sum[a] = r[3 + a];
+        e.sum_sq[a] = r[5 + a];
+    }
+    *out = e;
+    return LF2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// lf2_internal.cuh -- shared device arithmetic and launcher declarations of liblf2.
+//
+// Every kernel variant (one thread per site, z-streaming tiles, temporal blocking, ensemble)
+// performs the per-site update through the functions below, written with explicit
+// round-to-nearest intrinsics so that the compiler cannot contract or reorder them
+// differently in different kernels: all variants give bitwise identical results.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/lf2.h"
+
+namespace lf2 {
+
+constexpr int kMaxComp = 2;
+
+// ---------------------------------------------------------------- coefficient packs
+// FP64: the force enters only through dt*F, folded as
+//   dt F_a = a * nb_a - (dl * s2 + b0) * phi_a
+// with nb_a the sum of the 6 neighbours, s2 = sum_b phi_b^2 and
+//   a = dt/dx^2,  dl = dt lambda,  b0 = dt (6/dx^2 + m2 - lambda eta^2).
+struct Coef64 {
+    double a, dl, b0, dt;
+};
+
+// FP32: difference form of the Laplacian (sum_i (phi(x+-i) - phi(x))), which keeps the
+// small differences of a smooth field exact when |phi| ~ eta, then
+//   F_a = d_a * inv_dx2 - (lambda (s2 - eta^2) + m2) phi_a.
+struct Coef32 {
+    float inv_dx2, lam, eta2, m2, dt;
+};
+
+// Energy (always FP64).
+struct CoefE {
+    double inv_dx2, lam, eta2, m2, half_dt;
+};
+
+inline Coef64 make_coef64(const lf2_params &p, double dt) {
+    const double inv_dx2 = 1.0 / (p.dx * p.dx);
+    return Coef64{dt * inv_dx2, dt * p.lambda, dt * (6.0 * inv_dx2 + p.m2 - p.lambda * p.eta * p.eta), dt};
+}
+
+inline Coef32 make_coef32(const lf2_params &p, double dt) {
+    return Coef32{(float)(1.0 / (p.dx * p.dx)), (float)p.lambda, (float)(p.eta * p.eta), (float)p.m2, (float)dt};
+}
+
+inline CoefE make_coefE(const lf2_params &p) {
+    return CoefE{1.0 / (p.dx * p.dx), p.lambda, p.eta * p.eta, p.m2, 0.5 * p.dt};
+}
+
+// ------------------------------------------------------------------ per-site update
+// Neighbour values are passed in the fixed order -x, +x, -y, +y, -z, +z.
+
+// FP64 kick (+ drift).  pi <- pi + dt F(phi);  phi_out <- phi + dt pi.
+template <int NC>
+__device__ __forceinline__ void update_f64(const double (&c)[NC], const double (&xm)[NC], const double (&xp)[NC],
+                                           const double (&ym)[NC], const double (&yp)[NC], const double (&zm)[NC],
+                                           const double (&zp)[NC], double (&p)[NC], double (&out)[NC],
+                                           const Coef64 &k) {
+    double s2 = __dmul_rn(c[0], c[0]);
+#pragma unroll
+    for (int b = 1; b < NC; ++b) s2 = __fma_rn(c[b], c[b], s2);
+    const double g = __fma_rn(k.dl, s2, k.b0);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        const double nb = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(xm[a], xp[a]), ym[a]), yp[a]), zm[a]), zp[a]);
+        p[a] = __fma_rn(k.a, nb, __fma_rn(-g, c[a], p[a]));
+        out[a] = __fma_rn(k.dt, p[a], c[a]);
+    }
+}
+
+// FP32 force, difference form.
+template <int NC>
+__device__ __forceinline__ void force_f32(const float (&c)[NC], const float (&xm)[NC], const float (&xp)[NC],
+                                          const float (&ym)[NC], const float (&yp)[NC], const float (&zm)[NC],
+                                          const float (&zp)[NC], float (&F)[NC], const Coef32 &k) {
+    float s2 = __fmul_rn(c[0], c[0]);
+#pragma unroll
+    for (int b = 1; b < NC; ++b) s2 = __fmaf_rn(c[b], c[b], s2);
+    const float g = __fmaf_rn(k.lam, __fsub_rn(s2, k.eta2), k.m2);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        const float dx_ = __fadd_rn(__fsub_rn(xm[a], c[a]), __fsub_rn(xp[a], c[a]));
+        const float dy_ = __fadd_rn(__fsub_rn(ym[a], c[a]), __fsub_rn(yp[a], c[a]));
+        const float dz_ = __fadd_rn(__fsub_rn(zm[a], c[a]), __fsub_rn(zp[a], c[a]));
+        const float d = __fadd_rn(__fadd_rn(dx_, dy_), dz_);
+        F[a] = __fmaf_rn(d, k.inv_dx2, -__fmul_rn(g, c[a]));
+    }
+}
+
+// FP32 kick + drift; KAHAN selects the compensated drift
+//   y = dt pi - comp;  t = phi + y;  comp = (t - phi) - y;  phi_out = t.
+template <int NC, bool KAHAN>
+__device__ __forceinline__ void update_f32(const float (&c)[NC], const float (&xm)[NC], const float (&xp)[NC],
+                                           const float (&ym)[NC], const float (&yp)[NC], const float (&zm)[NC],
+                                           const float (&zp)[NC], float (&p)[NC], float (&cmp)[NC],
+                                           float (&out)[NC], const Coef32 &k) {
+    float F[NC];
+    force_f32<NC>(c, xm, xp, ym, yp, zm, zp, F, k);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        p[a] = __fmaf_rn(k.dt, F[a], p[a]);
+        if (KAHAN) {
+            const float y = __fmaf_rn(k.dt, p[a], -cmp[a]);
+            const float t = __fadd_rn(c[a], y);
+            cmp[a] = __fsub_rn(__fsub_rn(t, c[a]), y);
+            out[a] = t;
+        } else {
+            out[a] = __fmaf_rn(k.dt, p[a], c[a]);
+        }
+    }
+}
+
+// FP64 kick only (start of the staggered scheme): pi <- pi + dt' F(phi).
+template <int NC>
+__device__ __forceinline__ void kick_f64(const double (&c)[NC], const double (&xm)[NC], const double (&xp)[NC],
+                                         const double (&ym)[NC], const double (&yp)[NC], const double (&zm)[NC],
+                                         const double (&zp)[NC], double (&p)[NC], const Coef64 &k) {
+    double out[NC];
+    update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, out, k);
+}
+
+template <int NC>
+__device__ __forceinline__ void kick_f32(const float (&c)[NC], const float (&xm)[NC], const float (&xp)[NC],
+                                         const float (&ym)[NC], const float (&yp)[NC], const float (&zm)[NC],
+                                         const float (&zp)[NC], float (&p)[NC], const Coef32 &k) {
+    float F[NC];
+    force_f32<NC>(c, xm, xp, ym, yp, zm, zp, F, k);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) p[a] = __fmaf_rn(k.dt, F[a], p[a]);
+}
+
+// ----------------------------------------------------------------- geometry helpers
+struct Geom {
+    int nx, ny, nz;
+    long long sites;
+};
+
+__device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
+__device__ __forceinline__ int wrap_up(int i, int n) { return i == n - 1 ? 0 : i + 1; }
+
+// ------------------------------------------------------------------ host launchers
+// Arguments of one leapfrog pass over a lattice.
+struct StepArgs {
+    const void *phi;  // phi_n (storage type of prec)
+    void *phi_out;    // phi_{n+1} (not touched by a kick-only pass)
+    void *pi;         // updated in place
+    float *comp;      // Kahan compensation (F32_KAHAN), updated in place
+    Geom g;
+    int ncomp;
+    lf2_precision prec;
+    lf2_params p;
+    double dt;        // time step of this pass (the half-kick uses -dt/2)
+    bool drift;       // false: kick only
+};
+
+cudaError_t launch_site_step(const StepArgs &a, cudaStream_t s);
+
+// Streaming kernel (x-y tile, z-streaming); returns cudaErrorNotSupported when the shape
+// does not fit its constraints.
+bool stream_supported(const StepArgs &a, int tile_y, int zchunk);
+cudaError_t launch_stream_step(const StepArgs &a, int tile_y, int zchunk, int nsteps_hint, cudaStream_t s);
+
+// Energy: writes 8 doubles to `result` (device): kin, grad, pot (without dx^3),
+// sum[0], sum[1], sumsq[0], sumsq[1], unused.  `partials` holds kEnergyBlocks*8 doubles.
+constexpr int kEnergyBlocks = 152 * 4;
+constexpr int kEnergyThreads = 256;
+cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
+                          const lf2_params &p, double *partials, double *result, cudaStream_t s);
+
+// Conversions between host-side doubles and storage precision.
+cudaError_t launch_convert_from_f64(const double *src, void *dst, long long n, lf2_precision prec, cudaStream_t s);
+cudaError_t launch_convert_to_f64(const void *src, double *dst, long long n, lf2_precision prec, cudaStream_t s);
+
+}  // namespace lf2

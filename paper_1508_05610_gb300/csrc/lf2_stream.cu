@@ -1,0 +1,253 @@
+// lf2_stream.cu -- z-streaming leapfrog kernel: one HBM pass per step.
+//
+// A block owns an x-y tile of the lattice and walks a chunk of z-planes.  Each thread holds
+// 16 bytes of a row (4 floats or 2 doubles: S = 16 / (sizeof(R) * ncomp) sites) of three
+// consecutive planes in registers (z-1, z, z+1), so the z-neighbours of the 7-point stencil
+// cost nothing after the first load.  The current plane is also written to shared memory
+// with one halo row above and below the tile, from which the y-neighbours are read; the
+// x-neighbours come from the thread's own registers and from the adjacent lanes by warp
+// shuffle, with only the two edge lanes of a warp reading one site from global memory.
+// Periodic wrap (the torus of Sec. 3.3.1) is index arithmetic on plane, row and column.
+//
+// Requirements (else the one-thread-per-site kernel runs): rows of 16-byte multiples
+// (Nx * ncomp * sizeof(R) % 16 == 0) and Ny a multiple of the tile height.
+#include "lf2_internal.cuh"
+
+namespace lf2 {
+namespace {
+
+template <typename R>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using T = float4;
+    static constexpr int E = 4;
+};
+template <>
+struct Vec16<double> {
+    using T = double2;
+    static constexpr int E = 2;
+};
+
+template <typename R>
+__device__ __forceinline__ void ld16(const R *__restrict__ p, R (&v)[16 / sizeof(R)]) {
+    typename Vec16<R>::T t = __ldg(reinterpret_cast<const typename Vec16<R>::T *>(p));
+    memcpy(v, &t, 16);
+}
+
+template <typename R>
+__device__ __forceinline__ void ldcg16(const R *__restrict__ p, R (&v)[16 / sizeof(R)]) {
+    typename Vec16<R>::T t = __ldcg(reinterpret_cast<const typename Vec16<R>::T *>(p));
+    memcpy(v, &t, 16);
+}
+
+template <typename R>
+__device__ __forceinline__ void st16(R *__restrict__ p, const R (&v)[16 / sizeof(R)]) {
+    typename Vec16<R>::T t;
+    memcpy(&t, v, 16);
+    *reinterpret_cast<typename Vec16<R>::T *>(p) = t;
+}
+
+template <typename R>
+__device__ __forceinline__ R shfl_up1(R v) {
+    return __shfl_up_sync(0xffffffffu, v, 1);
+}
+template <typename R>
+__device__ __forceinline__ R shfl_dn1(R v) {
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+// MODE: 0 = FP32 plain drift, 1 = FP32 Kahan drift, 3 = FP64.
+template <typename R, int NC, int MODE, int BY, typename CoefT>
+__global__ void __launch_bounds__(32 * BY) k_stream(const R *__restrict__ phi, R *__restrict__ phi_out,
+                                                    R *__restrict__ pi, float *__restrict__ comp, Geom g, CoefT k,
+                                                    int zchunk) {
+    constexpr int E = 16 / sizeof(R);  // elements per thread
+    constexpr int S = E / NC;          // sites per thread
+    using VT = typename Vec16<R>::T;
+    __shared__ VT sm[2][BY + 2][32];
+
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int xs = (blockIdx.x * 32 + lane) * S;  // first site of this thread
+    const bool active = xs < g.nx;
+    const bool right_in_warp = (lane < 31) && (xs + S < g.nx);
+    const int y = blockIdx.y * BY + ty;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, g.nz);
+    const long long rowE = (long long)g.nx * NC;
+    const long long planeE = rowE * g.ny;
+    const long long col = (long long)xs * NC;
+    const long long off_y = (long long)y * rowE + col;
+    // halo rows of the tile: the row below (thread row 0) and above (last thread row)
+    int yh = -1, hslot = 0;
+    if (ty == 0) {
+        yh = wrap_dn(blockIdx.y * BY, g.ny);
+        hslot = 0;
+    } else if (ty == BY - 1) {
+        yh = wrap_up(y, g.ny);
+        hslot = BY + 1;
+    }
+    const long long off_h = (long long)yh * rowE + col;
+    // edge sites reached outside the warp
+    const int xl = wrap_dn(xs, g.nx);
+    const int xr = wrap_up(xs + S - 1, g.nx);
+    const long long off_l = (long long)y * rowE + (long long)xl * NC;
+    const long long off_r = (long long)y * rowE + (long long)xr * NC;
+
+    R below[E], cur[E], above[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) below[e] = cur[e] = above[e] = R(0);
+    if (active) {
+        ld16(phi + (long long)wrap_dn(z0, g.nz) * planeE + off_y, below);
+        ld16(phi + (long long)z0 * planeE + off_y, cur);
+    }
+
+    for (int z = z0; z < z1; ++z) {
+        const long long pz = (long long)z * planeE;
+        R halo[E], pv[E], cv[E], lft[NC], rgt[NC];
+        if (active) {
+            ld16(phi + (long long)wrap_up(z, g.nz) * planeE + off_y, above);
+            if (yh >= 0) ld16(phi + pz + off_h, halo);
+            ldcg16(pi + pz + off_y, pv);
+            if (MODE == 1) ldcg16(reinterpret_cast<const R *>(comp) + pz + off_y, cv);
+            if (lane == 0) {
+#pragma unroll
+                for (int a = 0; a < NC; ++a) lft[a] = __ldg(phi + pz + off_l + a);
+            }
+            if (!right_in_warp) {
+#pragma unroll
+                for (int a = 0; a < NC; ++a) rgt[a] = __ldg(phi + pz + off_r + a);
+            }
+        }
+        const int buf = (z - z0) & 1;
+        {
+            VT t;
+            memcpy(&t, cur, 16);
+            sm[buf][ty + 1][lane] = t;
+            if (yh >= 0) {
+                memcpy(&t, halo, 16);
+                sm[buf][hslot][lane] = t;
+            }
+        }
+        // x-neighbours across lanes
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            const R fromleft = shfl_up1(cur[(S - 1) * NC + a]);
+            const R fromright = shfl_dn1(cur[a]);
+            if (lane > 0) lft[a] = fromleft;
+            if (right_in_warp) rgt[a] = fromright;
+        }
+        __syncthreads();
+        R ymv[E], ypv[E];
+        {
+            VT t = sm[buf][ty][lane];
+            memcpy(ymv, &t, 16);
+            t = sm[buf][ty + 2][lane];
+            memcpy(ypv, &t, 16);
+        }
+        if (active) {
+            R outv[E];
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                R c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], o[NC];
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e = j * NC + a;
+                    c[a] = cur[e];
+                    xm[a] = (j == 0) ? lft[a] : cur[e - NC];
+                    xp[a] = (j == S - 1) ? rgt[a] : cur[e + NC];
+                    ym[a] = ymv[e];
+                    yp[a] = ypv[e];
+                    zm[a] = below[e];
+                    zp[a] = above[e];
+                    p[a] = pv[e];
+                    cm[a] = (MODE == 1) ? (float)cv[e] : 0.0f;
+                }
+                if constexpr (MODE == 3) {
+                    update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, o, k);
+                } else {
+                    update_f32<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, o, k);
+                }
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e = j * NC + a;
+                    outv[e] = o[a];
+                    pv[e] = p[a];
+                    if (MODE == 1) cv[e] = cm[a];
+                }
+            }
+            st16(phi_out + pz + off_y, outv);
+            st16(pi + pz + off_y, pv);
+            if (MODE == 1) st16(reinterpret_cast<R *>(comp) + pz + off_y, cv);
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            below[e] = cur[e];
+            cur[e] = above[e];
+        }
+    }
+}
+
+constexpr int kDefaultBY = 8;
+
+template <typename R, int NC, int MODE, int BY, typename CoefT>
+cudaError_t launch_t(const StepArgs &a, int zchunk, const CoefT &k, cudaStream_t s) {
+    constexpr int S = 16 / (int)sizeof(R) / NC;
+    dim3 block(32, BY);
+    dim3 grid((a.g.nx + 32 * S - 1) / (32 * S), a.g.ny / BY, (a.g.nz + zchunk - 1) / zchunk);
+    k_stream<R, NC, MODE, BY, CoefT><<<grid, block, 0, s>>>((const R *)a.phi, (R *)a.phi_out, (R *)a.pi, a.comp, a.g,
+                                                             k, zchunk);
+    return cudaGetLastError();
+}
+
+template <int BY>
+cudaError_t launch_by(const StepArgs &a, int zchunk, cudaStream_t s) {
+    if (a.prec == LF2_F64) {
+        const Coef64 k = make_coef64(a.p, a.dt);
+        return a.ncomp == 1 ? launch_t<double, 1, 3, BY>(a, zchunk, k, s) : launch_t<double, 2, 3, BY>(a, zchunk, k, s);
+    }
+    const Coef32 k = make_coef32(a.p, a.dt);
+    if (a.prec == LF2_F32_KAHAN)
+        return a.ncomp == 1 ? launch_t<float, 1, 1, BY>(a, zchunk, k, s) : launch_t<float, 2, 1, BY>(a, zchunk, k, s);
+    return a.ncomp == 1 ? launch_t<float, 1, 0, BY>(a, zchunk, k, s) : launch_t<float, 2, 0, BY>(a, zchunk, k, s);
+}
+
+int default_zchunk(const StepArgs &a, int by) {
+    // Enough blocks for several waves on 152 SMs, long enough chunks to amortise the two
+    // extra planes each chunk reads.
+    const int esz = a.prec == LF2_F64 ? 8 : 4;
+    const int S = 16 / esz / a.ncomp;
+    const long long tiles = (long long)((a.g.nx + 32 * S - 1) / (32 * S)) * (a.g.ny / by);
+    int zc = a.g.nz;
+    while (zc > 16 && tiles * ((a.g.nz + zc - 1) / zc) < 152 * 8) zc = (zc + 1) / 2;
+    return zc;
+}
+
+}  // namespace
+
+bool stream_supported(const StepArgs &a, int tile_y, int zchunk) {
+    const int by = tile_y ? tile_y : kDefaultBY;
+    if (by != 2 && by != 4 && by != 8 && by != 16) return false;
+    const int esz = a.prec == LF2_F64 ? 8 : 4;
+    if (((long long)a.g.nx * a.ncomp * esz) % 16) return false;
+    if (a.g.ny % by) return false;
+    if (zchunk < 0) return false;
+    if (!a.drift) return false;
+    // 16-byte alignment of every buffer
+    if (((uintptr_t)a.phi | (uintptr_t)a.phi_out | (uintptr_t)a.pi | (uintptr_t)a.comp) % 16) return false;
+    return true;
+}
+
+cudaError_t launch_stream_step(const StepArgs &a, int tile_y, int zchunk, int, cudaStream_t s) {
+    if (a.g.sites == 0) return cudaSuccess;
+    const int by = tile_y ? tile_y : kDefaultBY;
+    const int zc = zchunk > 0 ? zchunk : default_zchunk(a, by);
+    switch (by) {
+        case 2: return launch_by<2>(a, zc, s);
+        case 4: return launch_by<4>(a, zc, s);
+        case 8: return launch_by<8>(a, zc, s);
+        default: return launch_by<16>(a, zc, s);
+    }
+}
+
+}  // namespace lf2

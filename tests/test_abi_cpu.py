@@ -1,0 +1,141 @@
+"""CPU-only checks of the C ABI: the library builds, loads, exports every symbol declared in
+include/lf2.h, and validates arguments on calls that touch no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1508_05610_gb300 import build, lf2
+    build.build()
+    return lf2
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lf2.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lf2_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("lf2_lattice_create", "lf2_field_alloc", "lf2_leapfrog", "lf2_energy", "lf2_field_update_halo",
+                 "lf2_leapfrog_init", "lf2_field_upload", "lf2_field_download"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in declared_symbols():
+        assert hasattr(so, name), name
+
+
+def test_binding_covers_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert name in lib.SIGNATURES, name
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(lib):
+    assert lib.lf2_status_string(0) == "LF2_OK"
+    assert lib.lf2_status_string(5) == "LF2_ERR_TIMEOUT"
+    assert "sm_103a" in lib.lf2_version()
+
+
+def test_lattice_argument_checks(lib):
+    with pytest.raises(lib.LF2Error) as e:
+        lib.lf2_lattice_create([8, 8], dim=2)
+    assert e.value.status == lib.LF2_ERR_UNSUPPORTED
+    with pytest.raises(lib.LF2Error) as e:
+        lib.lf2_lattice_create([8, 8, 8, 8], dim=4)
+    assert e.value.status == lib.LF2_ERR_UNSUPPORTED
+    with pytest.raises(lib.LF2Error) as e:
+        lib.lf2_lattice_create([8, 8, 8], dim=1)
+    assert e.value.status == lib.LF2_ERR_INVALID
+    with pytest.raises(lib.LF2Error) as e:
+        lib.lf2_lattice_create([8, 0, 8])
+    assert e.value.status == lib.LF2_ERR_INVALID
+    with pytest.raises(lib.LF2Error) as e:
+        lib.lf2_lattice_create([8, 8, 8], halo=0)
+    assert e.value.status == lib.LF2_ERR_INVALID
+    with pytest.raises(lib.LF2Error) as e:
+        lib.lf2_lattice_create([1 << 14, 1 << 14, 1 << 14])
+    assert e.value.status == lib.LF2_ERR_INVALID
+    lat = lib.lf2_lattice_create([3, 4, 5])
+    assert lib.lf2_lattice_sites(lat) == 60
+    lib.lf2_lattice_destroy(lat)
+
+
+def test_field_argument_checks_before_any_device_call(lib):
+    lat = lib.lf2_lattice_create([4, 4, 4])
+    try:
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_field_alloc(lat, 3, lib.LF2_F64)
+        assert e.value.status == lib.LF2_ERR_UNSUPPORTED
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_field_alloc(lat, 0, lib.LF2_F64)
+        assert e.value.status == lib.LF2_ERR_INVALID
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_field_alloc(lat, 1, 7)
+        assert e.value.status == lib.LF2_ERR_INVALID
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_field_wrap(lat, 1, lib.LF2_F64, [0x1008])  # not 16-byte aligned
+        assert e.value.status == lib.LF2_ERR_INVALID
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_field_wrap(lat, 1, lib.LF2_F64, [0x1000, 0x2000, 0x3000])  # comp needs F32_KAHAN
+        assert e.value.status == lib.LF2_ERR_INVALID
+        # wrap touches no device memory: a borrowed field can be created and freed on the host
+        f = lib.lf2_field_wrap(lat, 2, lib.LF2_F32_KAHAN, [0x1000, 0x2000, 0x3000])
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_lattice_destroy(lat)
+        assert e.value.status == lib.LF2_ERR_STATE
+        assert lib.lf2_field_buffer(f, 0) == 0x1000 and lib.lf2_field_buffer(f, 2) == 0x3000
+        lib.lf2_field_update_halo(f)
+        g = lib.lf2_field_wrap(lat, 1, lib.LF2_F64, [0x1000])
+        p = lib.params()
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_leapfrog(f, g, p, 1)  # mismatched ncomp / precision
+        assert e.value.status == lib.LF2_ERR_INVALID
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_leapfrog(f, f, p, 1)
+        assert e.value.status == lib.LF2_ERR_INVALID
+        bad = lib.params(dx=0.0)
+        h = lib.lf2_field_wrap(lat, 1, lib.LF2_F64, [0x4000])
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_leapfrog(g, h, bad, 1)
+        assert e.value.status == lib.LF2_ERR_INVALID
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_leapfrog(g, h, p, -1)
+        assert e.value.status == lib.LF2_ERR_INVALID
+        for x in (f, g, h):
+            lib.lf2_field_free(x)
+    finally:
+        lib.lf2_lattice_destroy(lat)
+
+
+def test_alloc_failure_is_reported_not_hidden(lib, monkeypatch):
+    """Without a GPU (or with an injected failure) allocation reports an error status; there is
+    no host fallback."""
+    monkeypatch.setenv("LF2_FAULT", "alloc")
+    lat = lib.lf2_lattice_create([4, 4, 4])
+    try:
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_field_alloc(lat, 1, lib.LF2_F64)
+        assert e.value.status == lib.LF2_ERR_NOMEM
+    finally:
+        lib.lf2_lattice_destroy(lat)
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1508_05610_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, fn)).read()
+                bad = re.search(r"(from\s+oracle|import\s+oracle|oracle\.|lf2_oracle|\bora_[a-z]+\()", text)
+                assert bad is None, (os.path.join(dirpath, fn), bad and bad.group(0))

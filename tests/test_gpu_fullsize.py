@@ -1,0 +1,130 @@
+"""Parity at full workload sizes, in the launch configuration the benchmark times.
+
+The oracle cannot evolve a 256^3 or 1024^3 lattice in seconds, but one site after n steps
+depends only on the initial data within n sites of it.  So the oracle evolves the periodic
+(2h+1)^3 box cut around a sampled site (h >= n + 1) and its centre must match the GPU's value
+at that site.  Inputs are generated on the device by the seeded generator and the boxes are
+copied to the host from that same input array.
+"""
+import numpy as np
+import pytest
+
+from paper_1508_05610_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 10
+HALF = STEPS + 2
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1508_05610_gb300 import build, lf2
+    build.build()
+    lf2.load()
+    return torch, lf2
+
+
+def sample_sites(n, count, seed):
+    g = np.random.default_rng(seed)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (n - 1, 0, n // 2)]
+    pts += [tuple(int(v) for v in g.integers(0, n, 3)) for _ in range(count - len(pts))]
+    return pts
+
+
+def box_of(torch, field, center, half):
+    """(2 half + 1)^3 periodic box of a device field (nz, ny, nx, c) around center (x, y, z)."""
+    nz, ny, nx = field.shape[:3]
+    r = torch.arange(-half, half + 1, device=field.device)
+    zi = (center[2] + r) % nz
+    yi = (center[1] + r) % ny
+    xi = (center[0] + r) % nx
+    return field[zi][:, yi][:, :, xi].double().cpu().numpy()
+
+
+def run_wrapped(torch, lf2, phi_t, pi_t, prec, p, steps):
+    """Evolves device tensors in place through the C ABI (borrowed buffers); returns the tensor
+    that holds phi after the run (phi's front and back buffers swap every step)."""
+    nz, ny, nx, c = phi_t.shape
+    back = torch.empty_like(phi_t)
+    ptrs = [phi_t.data_ptr(), back.data_ptr()]
+    if prec == lf2.LF2_F32_KAHAN:
+        comp = torch.zeros_like(phi_t)
+        ptrs.append(comp.data_ptr())
+    lat = lf2.lf2_lattice_create((nx, ny, nz))
+    fphi = lf2.lf2_field_wrap(lat, c, prec, ptrs)
+    fpi = lf2.lf2_field_wrap(lat, c, prec, [pi_t.data_ptr()])
+    try:
+        stream = torch.cuda.current_stream()
+        lf2.lf2_leapfrog_init(fphi, fpi, p, stream)
+        lf2.lf2_leapfrog(fphi, fpi, p, steps, stream)
+        torch.cuda.synchronize()
+        front = lf2.lf2_field_buffer(fphi, 0)
+    finally:
+        lf2.lf2_field_free(fphi)
+        lf2.lf2_field_free(fpi)
+        lf2.lf2_lattice_destroy(lat)
+    return phi_t if front == phi_t.data_ptr() else back
+
+
+def check_boxes(torch, ora, phi0_t, phi_t, pi_t, kw, tol, seed):
+    n = phi0_t.shape[0]
+    worst = 0.0
+    for center in sample_sites(n, 8, seed):
+        box = box_of(torch, phi0_t, center, HALF)
+        bphi, bpi = ora.evolve(box, np.zeros_like(box), STEPS, half_kick=True, **kw)
+        scale = np.max(np.abs(bphi))
+        x, y, z = center
+        got_phi = phi_t[z, y, x].double().cpu().numpy()
+        got_pi = pi_t[z, y, x].double().cpu().numpy()
+        err = max(np.max(np.abs(got_phi - bphi[HALF, HALF, HALF])) / scale,
+                  np.max(np.abs(got_pi - bpi[HALF, HALF, HALF])) / max(np.max(np.abs(bpi)), 1e-300))
+        worst = max(worst, err)
+        assert err <= tol, (center, err)
+    return worst
+
+
+def test_256cube_complex_fp64_sampled(env, ora):
+    """256^3 complex phi^4, FP64, dt=0.05, lambda=eta=1, sigma=0.1: the benchmark lattice."""
+    torch, lf2 = env
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field_device(256, 256, 256, 2, sigma=0.1, seed=inputs.BASE_SEED)
+    phi = phi0.clone()
+    pi = torch.zeros_like(phi)
+    out = run_wrapped(torch, lf2, phi, pi, lf2.LF2_F64, lf2.params(**kw), STEPS)
+    check_boxes(torch, ora, phi0, out, pi, kw, 1e-12, seed=1)
+
+
+def test_256cube_complex_energy_of_inputs(env, ora):
+    """Full-lattice FP64 energy and checksums of seeded inputs (phi and a non-zero pi)."""
+    torch, lf2 = env
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(256, 256, 256, 2, sigma=0.1, seed=11)
+    pi0 = inputs.gaussian_field(256, 256, 256, 2, sigma=0.05, seed=12)
+    oe = ora.energy(phi0, pi0, **kw)
+    p = lf2.params(**kw)
+    for prec, tol in (("f64", 1e-12), ("f32k", 1e-6)):
+        with lf2.System((256, 256, 256), 2, prec) as s:
+            s.upload(phi0, pi0)
+            e = lf2.lf2_energy(s.phi, s.pi, p)
+        assert abs(e["total"] - oe["total"]) <= tol * abs(oe["total"]), prec
+        for a in range(2):
+            assert abs(e["sum_sq"][a] - oe["sum_sq"][a]) <= tol * oe["sum_sq"][a], prec
+
+
+def test_1024cube_real_grf_fp32_kahan_sampled(env, ora):
+    """1024^3 real phi^4 from a Gaussian random field with P(k) ~ k^-2 cut at pi/4, FP32 with
+    the compensated drift, dt=0.05: sampled sites within 1e-5 of the FP64 oracle after 10 steps,
+    starting from the same float32 initial values."""
+    torch, lf2 = env
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.grf_field_device(1024, sigma=0.1, seed=inputs.BASE_SEED, dtype=torch.float32)
+    phi = phi0.clone()
+    pi = torch.zeros_like(phi)
+    out = run_wrapped(torch, lf2, phi, pi, lf2.LF2_F32_KAHAN, lf2.params(**kw), STEPS)
+    check_boxes(torch, ora, phi0, out, pi, kw, 1e-5, seed=2)
+    del phi0, phi, pi, out
+    torch.cuda.empty_cache()

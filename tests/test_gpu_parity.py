@@ -1,0 +1,170 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances:
+  * FP64: relative 1e-12 of max|.| after 10 steps for phi and pi, and of |E| for the energy.
+    The two sides round differently (the kernels fold dt into the force and use FMA), each
+    step adds O(10) ulps of relative error, so 10 steps stay near 1e-15.
+  * Integer-valued fields with dx = dt = 1 and no potential: every operation is exact in FP64
+    and FP32 (values stay below 2^24), so all precisions must match bitwise.
+  * FP32 (Kahan or plain) vs the FP64 oracle: relative max error <= 1e-5 after 10 steps
+    (float32 rounding of the initial data is ~6e-8 relative, and the per-step force error
+    ~1e-7; 10 steps of the phi^4 dynamics amplify that by well under 100).
+"""
+import numpy as np
+import pytest
+
+from paper_1508_05610_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lf2():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1508_05610_gb300 import build, lf2 as binding
+    build.build()
+    binding.load()
+    return binding
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def run_gpu(lf2, phi0, pi0, steps, prec, kw, half_kick=True, kernel=None, tile_y=0, zchunk=0):
+    nz, ny, nx, c = phi0.shape
+    p = lf2.params(**kw)
+    with lf2.System((nx, ny, nz), c, prec) as s:
+        s.upload(phi0, pi0)
+        if half_kick:
+            lf2.lf2_leapfrog_init(s.phi, s.pi, p)
+        if kernel is None:
+            lf2.lf2_leapfrog(s.phi, s.pi, p, steps)
+        else:
+            lf2.lf2_leapfrog_ex(s.phi, s.pi, p, steps, kernel=kernel, tile_y=tile_y, zchunk=zchunk)
+        e = lf2.lf2_energy(s.phi, s.pi, p, ncomp=c)
+        phi, pi = s.download()
+    return phi, pi, e
+
+
+# ---------------------------------------------------------------- 32^3 real, FP64
+def test_cfg_32cube_fp64_every_step(lf2, ora):
+    """32^3 real phi^4, FP64, dx=1, dt=0.1, lambda=eta=1, phi0 ~ N(0, 0.1^2), pi0 = 0, 100 steps:
+    energy and checksums every step, fields after 10 and 100 steps."""
+    kw = dict(dx=1.0, dt=0.1, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(32, 32, 32, 1, sigma=0.1, seed=inputs.BASE_SEED)
+    pi0 = np.zeros_like(phi0)
+    p = lf2.params(**kw)
+    ophi, opi = ora.evolve(phi0, pi0, 0, half_kick=True, **kw)
+    with lf2.System((32, 32, 32), 1, "f64") as s:
+        s.upload(phi0, pi0)
+        lf2.lf2_leapfrog_init(s.phi, s.pi, p)
+        for n in range(101):
+            if n > 0:
+                lf2.lf2_leapfrog(s.phi, s.pi, p, 1)
+                ophi, opi = ora.evolve(ophi, opi, 1, **kw)
+            e = lf2.lf2_energy(s.phi, s.pi, p, ncomp=1)
+            oe = ora.energy(ophi, opi, **kw)
+            assert abs(e["total"] - oe["total"]) <= F64_TOL * abs(oe["total"]), n
+            for key in ("kinetic", "gradient", "potential"):
+                assert abs(e[key] - oe[key]) <= F64_TOL * abs(oe["total"]), (n, key)
+            scale = float(np.sum(np.abs(ophi)))
+            assert abs(e["sum"][0] - oe["sum"][0]) <= F64_TOL * scale, n
+            assert abs(e["sum_sq"][0] - oe["sum_sq"][0]) <= F64_TOL * oe["sum_sq"][0], n
+            if n in (10, 100):
+                phi, pi = s.download()
+                assert relmax(phi, ophi) <= F64_TOL * (1 if n == 10 else 100), n
+                assert relmax(pi, opi) <= F64_TOL * (1 if n == 10 else 100), n
+
+
+# ----------------------------------------------------- shapes x kernels, FP64 parity
+SHAPES = [
+    ((3, 4, 5), 1), ((3, 4, 5), 2), ((6, 10, 14), 1), ((6, 10, 14), 2),
+    ((40, 16, 9), 1),    # streaming: ragged warp (20 of 32 lanes)
+    ((34, 8, 6), 2),     # streaming complex FP64: two x tiles, second has 2 lanes
+    ((160, 8, 7), 1),    # streaming FP64 real: 64-site tiles, 3 tiles, last ragged
+    ((64, 24, 33), 2),   # z chunks with a ragged last chunk
+]
+
+
+@pytest.mark.parametrize("shape,ncomp", SHAPES)
+def test_fp64_parity_10_steps(lf2, ora, shape, ncomp):
+    nx, ny, nz = shape
+    kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.3, seed=101)
+    pi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=102)
+    ophi, opi = ora.evolve(phi0, pi0, 10, half_kick=True, **kw)
+    oe = ora.energy(ophi, opi, **kw)
+    phi, pi, e = run_gpu(lf2, phi0, pi0, 10, "f64", kw)
+    assert relmax(phi, ophi) <= F64_TOL
+    assert relmax(pi, opi) <= F64_TOL
+    assert abs(e["total"] - oe["total"]) <= F64_TOL * abs(oe["total"])
+
+
+# ---------------------------------------------------- integer data: bitwise, every path
+@pytest.mark.parametrize("prec", ["f64", "f32k", "f32"])
+@pytest.mark.parametrize("shape,ncomp", [((5, 4, 3), 1), ((8, 8, 6), 2), ((40, 16, 9), 1), ((96, 8, 5), 1),
+                                         ((34, 8, 6), 2)])
+def test_integer_fields_bitwise_all_precisions(lf2, ora, prec, shape, ncomp):
+    nx, ny, nz = shape
+    kw = dict(dx=1.0, dt=1.0, lam=0.0, eta=0.0, m2=0.0)
+    phi0 = inputs.integer_field(nx, ny, nz, ncomp, lo=-4, hi=4, seed=5)
+    pi0 = inputs.integer_field(nx, ny, nz, ncomp, lo=-4, hi=4, seed=6)
+    steps = 4
+    ophi, opi = ora.evolve(phi0, pi0, steps, half_kick=False, **kw)
+    assert np.max(np.abs(ophi)) < 2 ** 24 and np.max(np.abs(opi)) < 2 ** 24
+    for kernel in (lf2.LF2_KERNEL_SITE, lf2.LF2_KERNEL_AUTO):
+        phi, pi, _ = run_gpu(lf2, phi0, pi0, steps, prec, kw, half_kick=False, kernel=kernel)
+        assert np.array_equal(phi, ophi) and np.array_equal(pi, opi), (prec, kernel)
+
+
+# ------------------------------------------- every kernel variant gives the same bits
+@pytest.mark.parametrize("prec", ["f64", "f32k", "f32"])
+@pytest.mark.parametrize("shape,ncomp", [((64, 16, 12), 1), ((32, 16, 10), 2), ((96, 8, 9), 1)])
+def test_kernel_variants_bitwise_identical(lf2, prec, shape, ncomp):
+    nx, ny, nz = shape
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.5, seed=7)
+    pi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=8)
+    ref = run_gpu(lf2, phi0, pi0, 6, prec, kw, kernel=lf2.LF2_KERNEL_SITE)
+    for tile_y in (2, 4, 8, 16 if ny % 16 == 0 else 8):
+        for zchunk in (0, 1, 3, nz):
+            got = run_gpu(lf2, phi0, pi0, 6, prec, kw, kernel=lf2.LF2_KERNEL_STREAM, tile_y=tile_y, zchunk=zchunk)
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), (tile_y, zchunk)
+            assert got[2]["total"] == ref[2]["total"]
+
+
+# ------------------------------------------------------- FP32 against the FP64 oracle
+@pytest.mark.parametrize("prec", ["f32k", "f32"])
+@pytest.mark.parametrize("ncomp", [1, 2])
+def test_fp32_within_stated_error_of_fp64_oracle(lf2, ora, prec, ncomp):
+    nx, ny, nz = 32, 24, 20
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=inputs.BASE_SEED)
+    pi0 = np.zeros_like(phi0)
+    ophi, opi = ora.evolve(phi0, pi0, 10, half_kick=True, **kw)
+    oe = ora.energy(ophi, opi, **kw)
+    phi, pi, e = run_gpu(lf2, phi0, pi0, 10, prec, kw)
+    assert relmax(phi, ophi) <= 1e-5
+    assert relmax(pi, opi) <= 1e-5
+    assert abs(e["total"] - oe["total"]) <= 1e-5 * abs(oe["total"])
+
+
+def test_fp32_kahan_beats_plain_over_many_small_steps(lf2, ora):
+    """The compensated drift keeps phi's rounding error from growing with the step count.
+    A homogeneous field with no potential has F = 0 exactly, so pi stays 0.3125 and
+    phi_n = 1 + n dt pi; dt = 2^-9 and pi are exact in float32, so every error comes from the
+    drift's own rounding: plain FP32 accumulates it over 4000 steps, Kahan does not."""
+    nx, ny, nz = 8, 8, 8
+    kw = dict(dx=1.0, dt=2.0 ** -9, lam=0.0, eta=0.0, m2=0.0)
+    phi0 = np.full((nz, ny, nx, 1), 1.0)
+    pi0 = np.full_like(phi0, 0.3125)
+    steps = 4000
+    ophi, _ = ora.evolve(phi0, pi0, steps, half_kick=True, **kw)
+    ek = relmax(run_gpu(lf2, phi0, pi0, steps, "f32k", kw)[0], ophi)
+    ep = relmax(run_gpu(lf2, phi0, pi0, steps, "f32", kw)[0], ophi)
+    assert ek <= 1.2e-7 and ek < ep / 10, (ek, ep)
