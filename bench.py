@@ -113,7 +113,7 @@ class WrappedPair:
     def __init__(self, torch, lf2, prec, phi0):
         self.torch, self.lf2, self.prec = torch, lf2, lf2.PRECISIONS[prec]
         dtype = torch.float64 if prec == "f64" else torch.float32
-        self.phi = phi0.to(dtype).contiguous()
+        self.phi = phi0.to(dtype=dtype, copy=True).contiguous()
         self.back = torch.empty_like(self.phi)
         self.pi = torch.zeros_like(self.phi)
         ptrs = [self.phi.data_ptr(), self.back.data_ptr()]
