@@ -156,15 +156,16 @@ def test_fp32_within_stated_error_of_fp64_oracle(lf2, ora, prec, ncomp):
 
 def test_fp32_kahan_beats_plain_over_many_small_steps(lf2, ora):
     """The compensated drift keeps phi's rounding error from growing with the step count.
-    A homogeneous field with no potential has F = 0 exactly, so pi stays 0.3125 and
-    phi_n = 1 + n dt pi; dt = 2^-9 and pi are exact in float32, so every error comes from the
-    drift's own rounding: plain FP32 accumulates it over 4000 steps, Kahan does not."""
+    A homogeneous field with no potential has F = 0 exactly, so pi stays constant and
+    phi_n = 1 + n dt pi.  pi = float32(0.3) and dt = 2^-9 are exact in float32 (the oracle gets the
+    same values), but dt * pi has bits far below the ulp of phi, so every FP32 drift rounds:
+    plain FP32 accumulates that rounding over 4000 steps, the compensated drift does not."""
     nx, ny, nz = 8, 8, 8
     kw = dict(dx=1.0, dt=2.0 ** -9, lam=0.0, eta=0.0, m2=0.0)
     phi0 = np.full((nz, ny, nx, 1), 1.0)
-    pi0 = np.full_like(phi0, 0.3125)
+    pi0 = np.full_like(phi0, float(np.float32(0.3)))
     steps = 4000
     ophi, _ = ora.evolve(phi0, pi0, steps, half_kick=True, **kw)
     ek = relmax(run_gpu(lf2, phi0, pi0, steps, "f32k", kw)[0], ophi)
     ep = relmax(run_gpu(lf2, phi0, pi0, steps, "f32", kw)[0], ophi)
-    assert ek <= 1.2e-7 and ek < ep / 10, (ek, ep)
+    assert ek <= 2.4e-7 and ek < ep / 10, (ek, ep)
