@@ -176,6 +176,21 @@ lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int
  * synchronises `stream`. */
 lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream);
 
+/* lf2_energy for callers that cannot allocate device memory.  The paper has no counterpart;
+ * this entry point exists for callers whose device allocator belongs to someone else (a memory
+ * pool or host framework that forbids cudaMalloc while it runs) or that must make no
+ * allocation call at all.  lf2_energy allocates scratch and a pinned result buffer on its
+ * first call for a field; this variant allocates nothing: no cudaMalloc, cudaFree, pinned-host
+ * or library allocation.  Its scratch is one fixed array inside the library (608 x 8 + 8
+ * doubles, 39 KB) that every GPU which loads the library holds until the process exits.  The
+ * reduction's grid is fixed, so every lattice fits; if the scratch needed ever exceeded the
+ * array, the call would return LF2_ERR_UNSUPPORTED with a message.  The first call on a device
+ * looks up the array's device address (make it before any stream capture).  All calls share
+ * the array: calls whose work overlaps on the GPU (different streams, or several host
+ * threads) race and must be serialised by the caller.  Arguments, result and synchronisation
+ * are those of lf2_energy; the result is copied into *out. */
+lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream);
+
 /* ------------------------------------------------------------------- utilities */
 
 const char *lf2_status_string(lf2_status s);

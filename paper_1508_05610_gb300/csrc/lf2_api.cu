@@ -433,4 +433,42 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
     return LF2_OK;
 }
 
+lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream) {
+    lf2_status st = check_pair(phi, pi);
+    if (st == LF2_OK) st = check_params(p);
+    if (st != LF2_OK) return st;
+    if (!out) return fail(LF2_ERR_INVALID, "output pointer is NULL");
+    // The reduction writes one partial per block of its fixed grid, then 8 results.
+    const long long needed = (long long)kEnergyBlocks * 8 + 8;
+    if (needed > kEnergyNoallocDoubles)
+        return fail(LF2_ERR_UNSUPPORTED, "energy reduction needs %lld scratch doubles, the fixed array holds %d",
+                    needed, kEnergyNoallocDoubles);
+    double *scratch = nullptr;
+    LF2_CUDA(energy_noalloc_scratch(&scratch), "cudaGetSymbolAddress(energy scratch)");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *partials = scratch;
+    double *result = scratch + kEnergyBlocks * 8;
+    // Every slot read below is written earlier in the same call, so nothing left over from a
+    // previous call is used and nothing needs clearing.
+    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[0], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
+                           result, s),
+             "energy launch");
+    double r[8];
+    LF2_CUDA(cudaMemcpyAsync(r, result, sizeof r, cudaMemcpyDeviceToHost, s), "energy copy");
+    LF2_CUDA(cudaStreamSynchronize(s), "energy sync");
+    const double vol = p->dx * p->dx * p->dx;
+    lf2_energy_t e;
+    memset(&e, 0, sizeof e);
+    e.kinetic = vol * r[0];
+    e.gradient = vol * r[1];
+    e.potential = vol * r[2];
+    e.total = e.kinetic + e.gradient + e.potential;
+    for (int a = 0; a < phi->ncomp; ++a) {
+        e.sum[a] = r[3 + a];
+        e.sum_sq[a] = r[5 + a];
+    }
+    *out = e;
+    return LF2_OK;
+}
+
 }  // extern "C"

@@ -13,6 +13,8 @@
 // grid-stride pass over sites leaves one partial per block (a scratch array of
 // kEnergyBlocks x 8 doubles), then one block sums the partials.  The scratch array lives in
 // global memory owned by the caller of launch_energy.
+#include <mutex>
+
 #include "lf2_internal.cuh"
 
 namespace lf2 {
@@ -115,6 +117,40 @@ cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int nc
     const CoefE k = make_coefE(p);
     if (prec == LF2_F64) return launch_typed<double>(phi, pi, g, ncomp, k, partials, result, s);
     return launch_typed<float>(phi, pi, g, ncomp, k, partials, result, s);
+}
+
+// ------------------------------------------------- fixed scratch for lf2_energy_noalloc
+// Some callers cannot allocate device memory: code that runs while a memory pool or another
+// framework owns the device allocator, or that must not make allocation calls at all.
+// lf2_energy allocates its partial-sum scratch on first use; lf2_energy_noalloc uses this
+// file-scope array instead.  Every GPU that loads the library holds it until process exit.
+// It holds the per-block partials of the reduction's fixed grid plus the 8 results; the grid
+// does not depend on the lattice, so the capacity is a constant.
+static __device__ __align__(256) double g_energy_noalloc[kEnergyNoallocDoubles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+// The device address of g_energy_noalloc on the current device.  The first call on a device
+// asks the runtime for it (host code cannot use the array's name as a device address) and
+// caches it; later calls only read the cache.
+cudaError_t energy_noalloc_scratch(double **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *addr = nullptr;
+        e = cudaGetSymbolAddress(&addr, g_energy_noalloc);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<double *>(addr);
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
 }
 
 }  // namespace lf2

@@ -170,6 +170,10 @@ constexpr int kEnergyThreads = 256;
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
                           const lf2_params &p, double *partials, double *result, cudaStream_t s);
 
+// Fixed-size scratch of lf2_energy_noalloc: kEnergyBlocks*8 partials + 8 results (39 KB).
+constexpr int kEnergyNoallocDoubles = kEnergyBlocks * 8 + 8;
+cudaError_t energy_noalloc_scratch(double **out);
+
 // Conversions between host-side doubles and storage precision.
 cudaError_t launch_convert_from_f64(const double *src, void *dst, long long n, lf2_precision prec, cudaStream_t s);
 cudaError_t launch_convert_to_f64(const void *src, double *dst, long long n, lf2_precision prec, cudaStream_t s);

@@ -70,6 +70,7 @@ SIGNATURES = {
     "lf2_leapfrog": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, _vp],
     "lf2_leapfrog_ex": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, ctypes.POINTER(lf2_step_config), _vp],
     "lf2_energy": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
+    "lf2_energy_noalloc": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
     "lf2_status_string": [ctypes.c_int],
     "lf2_last_error": [],
     "lf2_version": [],
@@ -186,6 +187,13 @@ def lf2_leapfrog_ex(phi, pi, p: lf2_params, nsteps, kernel=LF2_KERNEL_AUTO, tile
 def lf2_energy(phi, pi, p: lf2_params, stream=None, ncomp=2) -> dict:
     e = lf2_energy_t()
     _call("lf2_energy", phi, pi, ctypes.byref(p), ctypes.byref(e), _stream_ptr(stream))
+    return e.as_dict(ncomp)
+
+
+def lf2_energy_noalloc(phi, pi, p: lf2_params, stream=None, ncomp=2) -> dict:
+    """lf2_energy without any allocation (fixed scratch inside the library)."""
+    e = lf2_energy_t()
+    _call("lf2_energy_noalloc", phi, pi, ctypes.byref(p), ctypes.byref(e), _stream_ptr(stream))
     return e.as_dict(ncomp)
 
 
