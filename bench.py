@@ -41,6 +41,27 @@ KW = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
 WORKLOAD = "phi4 complex 256^3 periodic lattice, dt=0.05, lambda=eta=1, sigma=0.1 Gaussian init"
 BYTES_PER_SITE = {"f64": 8 * NCOMP * 4, "f32k": 4 * NCOMP * 6, "f32": 4 * NCOMP * 4}
 FALLBACK_HBM_GBS = 6800.0
+# FP64 is bound by the FP64 pipe on GB300: the nominal 1.25 TFLOP/s FP64 rate is 2 DFMA per SM
+# per clock x 152 SMs x 2.07 GHz = 629 G DP instructions/s.  The FP64 step issues 10 DP
+# instructions per real site and 19 per complex site (lf2_internal.cuh, update_f64).
+FP64_PEAK_GINST = 2 * 152 * 2.07
+DP_INSTR_PER_SITE = {1: 10, 2: 19}
+CSRC = os.path.join(ROOT, "paper_1508_05610_gb300", "csrc")
+
+
+def measured_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            entry = json.load(f)[key]
+        h = hashlib.sha256()
+        for name in entry["sources"]:
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(f.read())
+        return entry["bytes"] if h.hexdigest()[:16] == entry["src_sha"] else None
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def peaks():
@@ -253,13 +274,20 @@ def run_gpu(args):
     def gsu(t):
         return sites * world * args.steps / t / 1e9
 
-    def roof(prec, t):
+    def roof(prec, t, traffic_key):
         per_launch = t / args.steps
         achieved = BYTES_PER_SITE[prec] * sites / per_launch / 1e9
-        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": None,
-                "peak_source": f"{peak_src} HBM copy bandwidth",
-                "bytes_per_site_update": BYTES_PER_SITE[prec]}
+        hbm = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+               "frac": round(achieved / hbm_peak, 4), "traffic": measured_traffic(traffic_key),
+               "peak_source": f"{peak_src} HBM copy bandwidth",
+               "bytes_per_site_update": BYTES_PER_SITE[prec]}
+        if prec != "f64":
+            return hbm
+        ginst = DP_INSTR_PER_SITE[NCOMP] * sites / per_launch / 1e9
+        return {"bound": "alu", "achieved": round(ginst, 1), "peak": round(FP64_PEAK_GINST, 1),
+                "unit": "G FP64 instr/s", "frac": round(ginst / FP64_PEAK_GINST, 4),
+                "traffic": hbm["traffic"], "peak_source": "nominal FP64 rate 1.25 TFLOP/s = 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
+                "dp_instr_per_site_update": DP_INSTR_PER_SITE[NCOMP], "hbm": {k: hbm[k] for k in ("achieved", "peak", "frac")}}
 
     t64, t32 = results["f64"], results["f32k"]
     line = {
@@ -269,9 +297,9 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD + ", FP64, one step per HBM pass (plain path)", "lattice": [N, N, N],
                    "ncomp": NCOMP, "sites": sites, "precision": "f64", "parallelism": f"replicas x{world}",
                    "l2_policy": "state 805 MB > 129 MB L2; no flush needed"},
-        "roofline": roof("f64", t64),
+        "roofline": roof("f64", t64, "k_stream_f64_c2_256"),
         "fp32_kahan": {"value": round(gsu(t32), 3), "unit": UNIT, "ms_per_step": round(t32 / args.steps * 1e3, 5),
-                       "roofline": roof("f32k", t32), "speedup_vs_fp64": round(t64 / t32, 3),
+                       "roofline": roof("f32k", t32, "k_stream_f32k_c2_256"), "speedup_vs_fp64": round(t64 / t32, 3),
                        "error_vs_fp64": err},
         "e2e": {"value": round(sites * world * args.steps / t_e2e / 1e9, 3), "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": (state_bytes + 64) / args.steps,
@@ -302,10 +330,10 @@ def oracle_rate(nz_slab, steps, threads):
 
 def cpu_baseline():
     threads = os.cpu_count() or 1
-    nz_slab, steps = 64, 20
+    nz_slab, steps = 256, 100
     v, dt = oracle_rate(nz_slab, steps, threads)
     return {"value": round(v, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"FP64 oracle, {steps} steps of a 256x256x{nz_slab} complex slab of the workload "
+            "sample": f"FP64 oracle, {steps} steps of the 256x256x{nz_slab} complex lattice "
                       f"(OpenMP over z-planes), {dt:.1f} s"}
 
 
