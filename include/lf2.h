@@ -94,9 +94,11 @@ typedef enum {
 
 typedef struct {
     int kernel; /* lf2_kernel */
+    int tile_x; /* output sites of the x-y tile along x (TBLOCK); 0 = default */
     int tile_y; /* rows of the x-y tile (STREAM, TBLOCK); 0 = default */
     int zchunk; /* z-planes per block (STREAM, TBLOCK); 0 = default */
-    int depth;  /* temporal-blocking depth, steps fused per pass (TBLOCK); 0 = default */
+    int depth;  /* temporal-blocking depth, steps fused per pass: 2, 3, 4, 6 or 8 (TBLOCK); 0 = 4 */
+    int cx;     /* adjacent x-columns per thread, 1 or 2 (TBLOCK); 0 = default */
 } lf2_step_config;
 
 /* ---------------------------------------------------------------------- lattice */
@@ -126,18 +128,22 @@ lf2_status lf2_field_alloc(lf2_lattice lat, int ncomp, lf2_precision prec, lf2_f
 
 /* Like lf2_field_alloc, but the buffers are borrowed from the caller (for example torch
  * tensors), who must keep them alive and contiguous until lf2_field_free.  dev_ptrs[0] is
- * the value buffer; dev_ptrs[1] (optional) the phi back buffer; dev_ptrs[2] (optional,
- * LF2_F32_KAHAN only) the float compensation buffer.  nptrs is 1, 2 or 3.  Every pointer
- * must be 16-byte aligned.  Buffers not given are allocated by the library when needed. */
+ * the value buffer; dev_ptrs[1] (optional) the back buffer; dev_ptrs[2] and dev_ptrs[3]
+ * (optional, LF2_F32_KAHAN only) the float compensation buffer and its back buffer.  nptrs is
+ * 1 to 4.  Every pointer must be 16-byte aligned.  Buffers not given are allocated by the
+ * library when first needed (temporal blocking needs back buffers for pi and the compensation
+ * as well as for phi). */
 lf2_status lf2_field_wrap(lf2_lattice lat, int ncomp, lf2_precision prec, void *const *dev_ptrs,
                           int nptrs, lf2_field *out);
 
 /* Frees the field and every buffer the library allocated for it. */
 lf2_status lf2_field_free(lf2_field f);
 
-/* Device address of one of the field's buffers: which = 0 the current value buffer (it
- * changes after each lf2_leapfrog step, because phi's front and back buffers swap), 1 the
- * back buffer, 2 the compensation buffer.  *out is NULL if that buffer does not exist. */
+/* Device address of one of the field's buffers: which = 0 the current value buffer, 1 the
+ * back buffer, 2 the current compensation buffer, 3 its back buffer.  Front and back swap
+ * as the leapfrog runs (phi's every step; pi's and the compensation's after each
+ * temporal-blocking pass), so ask again after each call.  *out is NULL if that buffer does
+ * not exist. */
 lf2_status lf2_field_buffer(lf2_field f, int which, void **out);
 
 /* Copies sites*ncomp doubles from host memory (the layout above) into the field, converting

@@ -34,11 +34,12 @@ struct lf2_field_s {
     lf2_precision prec = LF2_F64;
     size_t esize = 0;  // bytes per stored element
     long long count = 0;  // sites * ncomp
-    void *val[2] = {nullptr, nullptr};
+    void *val[2] = {nullptr, nullptr};  // value buffers; val[front] is current
     bool own_val[2] = {false, false};
     int front = 0;
-    float *comp = nullptr;
-    bool own_comp = false;
+    float *comp[2] = {nullptr, nullptr};  // Kahan compensation of phi (F32_KAHAN); comp[cfront] current
+    bool own_comp[2] = {false, false};
+    int cfront = 0;
     double *energy_scratch = nullptr;  // kEnergyBlocks*8 partials + 8 results (device)
     double *energy_host = nullptr;     // 8 pinned doubles
 };
@@ -92,26 +93,47 @@ lf2_status check_pair(lf2_field phi, lf2_field pi) {
     return LF2_OK;
 }
 
+bool fault_injected(const char *what) {
+    const char *f = getenv("LF2_FAULT");
+    return f && !strcmp(f, what);
+}
+
+lf2_status alloc_back(lf2_field f, const char *what) {
+    if (f->val[1 - f->front]) return LF2_OK;
+    if (fault_injected("alloc")) return fail(LF2_ERR_NOMEM, "allocation failure injected by LF2_FAULT=alloc");
+    void *b = nullptr;
+    const size_t bytes = (size_t)f->count * f->esize;
+    LF2_CUDA(cudaMalloc(&b, bytes ? bytes : 16), what);
+    f->val[1 - f->front] = b;
+    f->own_val[1 - f->front] = true;
+    return LF2_OK;
+}
+
+lf2_status alloc_comp(lf2_field phi, int which, cudaStream_t s) {
+    if (phi->comp[which]) return LF2_OK;
+    if (fault_injected("alloc")) return fail(LF2_ERR_NOMEM, "allocation failure injected by LF2_FAULT=alloc");
+    void *c = nullptr;
+    const size_t cb = (size_t)phi->count * sizeof(float);
+    LF2_CUDA(cudaMalloc(&c, cb ? cb : 16), "cudaMalloc(compensation)");
+    phi->comp[which] = (float *)c;
+    phi->own_comp[which] = true;
+    LF2_CUDA(cudaMemsetAsync(c, 0, cb, s), "cudaMemsetAsync(compensation)");
+    return LF2_OK;
+}
+
 // Back buffer and compensation of a field used as phi.
 lf2_status ensure_dynamic(lf2_field phi, cudaStream_t s) {
-    const size_t bytes = (size_t)phi->count * phi->esize;
-    if (!phi->val[1 - phi->front]) {
-        void *b = nullptr;
-        if (getenv("LF2_FAULT") && !strcmp(getenv("LF2_FAULT"), "alloc"))
-            return fail(LF2_ERR_NOMEM, "allocation failure injected by LF2_FAULT=alloc");
-        LF2_CUDA(cudaMalloc(&b, bytes ? bytes : 16), "cudaMalloc(phi back buffer)");
-        phi->val[1 - phi->front] = b;
-        phi->own_val[1 - phi->front] = true;
-    }
-    if (phi->prec == LF2_F32_KAHAN && !phi->comp) {
-        void *c = nullptr;
-        const size_t cb = (size_t)phi->count * sizeof(float);
-        LF2_CUDA(cudaMalloc(&c, cb ? cb : 16), "cudaMalloc(compensation)");
-        phi->comp = (float *)c;
-        phi->own_comp = true;
-        LF2_CUDA(cudaMemsetAsync(c, 0, cb, s), "cudaMemsetAsync(compensation)");
-    }
-    return LF2_OK;
+    lf2_status st = alloc_back(phi, "cudaMalloc(phi back buffer)");
+    if (st == LF2_OK && phi->prec == LF2_F32_KAHAN) st = alloc_comp(phi, phi->cfront, s);
+    return st;
+}
+
+// Temporal blocking also writes pi and the compensation out of place.
+lf2_status ensure_tblock(lf2_field phi, lf2_field pi, cudaStream_t s) {
+    lf2_status st = ensure_dynamic(phi, s);
+    if (st == LF2_OK) st = alloc_back(pi, "cudaMalloc(pi back buffer)");
+    if (st == LF2_OK && phi->prec == LF2_F32_KAHAN) st = alloc_comp(phi, 1 - phi->cfront, s);
+    return st;
 }
 
 lf2_status ensure_energy_scratch(lf2_field f) {
@@ -132,14 +154,30 @@ StepArgs step_args(lf2_field phi, lf2_field pi, const lf2_params *p, double dt, 
     StepArgs a;
     a.phi = phi->val[phi->front];
     a.phi_out = phi->val[1 - phi->front];
-    a.pi = pi->val[0];
-    a.comp = phi->comp;
+    a.pi = pi->val[pi->front];
+    a.comp = phi->comp[phi->cfront];
     a.g = geom_of(phi->lat);
     a.ncomp = phi->ncomp;
     a.prec = phi->prec;
     a.p = *p;
     a.dt = dt;
     a.drift = drift;
+    return a;
+}
+
+TbArgs tb_args(lf2_field phi, lf2_field pi, const lf2_params *p) {
+    TbArgs a;
+    a.phi = phi->val[phi->front];
+    a.phi_out = phi->val[1 - phi->front];
+    a.pi = pi->val[pi->front];
+    a.pi_out = pi->val[1 - pi->front];
+    a.comp = phi->comp[phi->cfront];
+    a.comp_out = phi->comp[1 - phi->cfront];
+    a.g = geom_of(phi->lat);
+    a.ncomp = phi->ncomp;
+    a.prec = phi->prec;
+    a.p = *p;
+    a.dt = p->dt;
     return a;
 }
 
@@ -238,8 +276,8 @@ lf2_status lf2_field_wrap(lf2_lattice lat, int ncomp, lf2_precision prec, void *
                           lf2_field *out) {
     lf2_status st = new_field(lat, ncomp, prec, out);
     if (st != LF2_OK) return st;
-    if (!dev_ptrs || nptrs < 1 || nptrs > 3) return fail(LF2_ERR_INVALID, "nptrs must be 1, 2 or 3");
-    if (nptrs == 3 && prec != LF2_F32_KAHAN) return fail(LF2_ERR_INVALID, "a compensation buffer needs LF2_F32_KAHAN");
+    if (!dev_ptrs || nptrs < 1 || nptrs > 4) return fail(LF2_ERR_INVALID, "nptrs must be 1 to 4");
+    if (nptrs >= 3 && prec != LF2_F32_KAHAN) return fail(LF2_ERR_INVALID, "a compensation buffer needs LF2_F32_KAHAN");
     for (int i = 0; i < nptrs; ++i) {
         if (!dev_ptrs[i]) return fail(LF2_ERR_INVALID, "dev_ptrs[%d] is NULL", i);
         if ((uintptr_t)dev_ptrs[i] % 16) return fail(LF2_ERR_INVALID, "dev_ptrs[%d] is not 16-byte aligned", i);
@@ -253,7 +291,8 @@ lf2_status lf2_field_wrap(lf2_lattice lat, int ncomp, lf2_precision prec, void *
     f->count = lat->sites * ncomp;
     f->val[0] = dev_ptrs[0];
     if (nptrs >= 2) f->val[1] = dev_ptrs[1];
-    if (nptrs >= 3) f->comp = (float *)dev_ptrs[2];
+    if (nptrs >= 3) f->comp[0] = (float *)dev_ptrs[2];
+    if (nptrs >= 4) f->comp[1] = (float *)dev_ptrs[3];
     lat->users++;
     *out = f;
     return LF2_OK;
@@ -263,7 +302,8 @@ lf2_status lf2_field_free(lf2_field f) {
     if (!f) return fail(LF2_ERR_INVALID, "field is NULL");
     for (int i = 0; i < 2; ++i)
         if (f->own_val[i] && f->val[i]) cudaFree(f->val[i]);
-    if (f->own_comp && f->comp) cudaFree(f->comp);
+    for (int i = 0; i < 2; ++i)
+        if (f->own_comp[i] && f->comp[i]) cudaFree(f->comp[i]);
     if (f->energy_scratch) cudaFree(f->energy_scratch);
     if (f->energy_host) cudaFreeHost(f->energy_host);
     f->lat->users--;
@@ -276,8 +316,9 @@ lf2_status lf2_field_buffer(lf2_field f, int which, void **out) {
     switch (which) {
         case 0: *out = f->val[f->front]; break;
         case 1: *out = f->val[1 - f->front]; break;
-        case 2: *out = f->comp; break;
-        default: return fail(LF2_ERR_INVALID, "which must be 0, 1 or 2");
+        case 2: *out = f->comp[f->cfront]; break;
+        case 3: *out = f->comp[1 - f->cfront]; break;
+        default: return fail(LF2_ERR_INVALID, "which must be 0, 1, 2 or 3");
     }
     return LF2_OK;
 }
@@ -304,8 +345,8 @@ lf2_status lf2_field_upload(lf2_field f, const double *host, void *stream) {
                 return cuda_fail(e, "upload");
             }
         }
-        if (f->comp) {
-            cudaError_t e = cudaMemsetAsync(f->comp, 0, total * sizeof(float), s);
+        if (f->comp[f->cfront]) {
+            cudaError_t e = cudaMemsetAsync(f->comp[f->cfront], 0, total * sizeof(float), s);
             if (e != cudaSuccess) {
                 cudaFree(stage);
                 return cuda_fail(e, "reset compensation");
@@ -316,7 +357,8 @@ lf2_status lf2_field_upload(lf2_field f, const double *host, void *stream) {
         if (e != cudaSuccess) return cuda_fail(e, "upload sync");
         return LF2_OK;
     }
-    if (f->comp) LF2_CUDA(cudaMemsetAsync(f->comp, 0, total * sizeof(float), s), "reset compensation");
+    if (f->comp[f->cfront])
+        LF2_CUDA(cudaMemsetAsync(f->comp[f->cfront], 0, total * sizeof(float), s), "reset compensation");
     LF2_CUDA(cudaStreamSynchronize(s), "upload sync");
     return LF2_OK;
 }
@@ -375,25 +417,50 @@ lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int
     if (st != LF2_OK) return st;
     if (nsteps < 0) return fail(LF2_ERR_INVALID, "nsteps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
-    st = ensure_dynamic(phi, s);
-    if (st != LF2_OK) return st;
     int kernel = cfg ? cfg->kernel : LF2_KERNEL_AUTO;
+    if (kernel < LF2_KERNEL_AUTO || kernel > LF2_KERNEL_TBLOCK) return fail(LF2_ERR_INVALID, "unknown kernel %d", kernel);
     const int tile_y = cfg ? cfg->tile_y : 0;
     const int zchunk = cfg ? cfg->zchunk : 0;
-    if (kernel < LF2_KERNEL_AUTO || kernel > LF2_KERNEL_TBLOCK) return fail(LF2_ERR_INVALID, "unknown kernel %d", kernel);
-    {
-        const StepArgs probe = step_args(phi, pi, p, p->dt, true);
-        if (kernel == LF2_KERNEL_AUTO) kernel = stream_supported(probe, 0, 0) ? LF2_KERNEL_STREAM : LF2_KERNEL_SITE;
-        if (kernel == LF2_KERNEL_STREAM && !stream_supported(probe, tile_y, zchunk))
-            return fail(LF2_ERR_UNSUPPORTED, "streaming kernel does not fit this lattice/config");
-        if (kernel == LF2_KERNEL_TBLOCK) return fail(LF2_ERR_UNSUPPORTED, "temporal blocking not built yet");
-    }
-    for (int n = 0; n < nsteps; ++n) {
+    st = (kernel == LF2_KERNEL_TBLOCK) ? ensure_tblock(phi, pi, s) : ensure_dynamic(phi, s);
+    if (st != LF2_OK) return st;
+
+    // one-step kernel used for single steps (and for what temporal blocking leaves over)
+    const StepArgs probe = step_args(phi, pi, p, p->dt, true);
+    const bool stream_ok = stream_supported(probe, kernel == LF2_KERNEL_STREAM ? tile_y : 0,
+                                            kernel == LF2_KERNEL_STREAM ? zchunk : 0);
+    if (kernel == LF2_KERNEL_STREAM && !stream_ok)
+        return fail(LF2_ERR_UNSUPPORTED, "streaming kernel does not fit this lattice/config");
+    const bool use_stream = (kernel == LF2_KERNEL_STREAM || kernel == LF2_KERNEL_AUTO || kernel == LF2_KERNEL_TBLOCK) &&
+                            stream_ok;
+    auto one_step = [&]() -> lf2_status {
         const StepArgs a = step_args(phi, pi, p, p->dt, true);
-        cudaError_t e = (kernel == LF2_KERNEL_STREAM) ? launch_stream_step(a, tile_y, zchunk, nsteps, s)
-                                                      : launch_site_step(a, s);
+        cudaError_t e = use_stream ? launch_stream_step(a, kernel == LF2_KERNEL_STREAM ? tile_y : 0,
+                                                        kernel == LF2_KERNEL_STREAM ? zchunk : 0, 1, s)
+                                   : launch_site_step(a, s);
         if (e != cudaSuccess) return cuda_fail(e, "leapfrog launch");
         phi->front = 1 - phi->front;
+        return LF2_OK;
+    };
+
+    int done = 0;
+    if (kernel == LF2_KERNEL_TBLOCK) {
+        TbConfig c{cfg->depth, cfg->cx, cfg->tile_x, tile_y, zchunk};
+        TbArgs ta = tb_args(phi, pi, p);
+        if (!tblock_supported(ta, c))
+            return fail(LF2_ERR_UNSUPPORTED, "temporal blocking config (depth %d, cx %d, tile %dx%d) does not fit",
+                        c.depth, c.cx, c.tile_x, c.tile_y);
+        for (; done + c.depth <= nsteps; done += c.depth) {
+            ta = tb_args(phi, pi, p);
+            cudaError_t e = launch_tblock(ta, c, s);
+            if (e != cudaSuccess) return cuda_fail(e, "temporal-blocking launch");
+            phi->front = 1 - phi->front;
+            pi->front = 1 - pi->front;
+            if (phi->prec == LF2_F32_KAHAN) phi->cfront = 1 - phi->cfront;
+        }
+    }
+    for (; done < nsteps; ++done) {
+        st = one_step();
+        if (st != LF2_OK) return st;
     }
     return LF2_OK;
 }
@@ -412,7 +479,7 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
     cudaStream_t s = (cudaStream_t)stream;
     double *partials = phi->energy_scratch;
     double *result = phi->energy_scratch + kEnergyBlocks * 8;
-    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[0], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
+    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
                            result, s),
              "energy launch");
     LF2_CUDA(cudaMemcpyAsync(phi->energy_host, result, 8 * sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
@@ -450,7 +517,7 @@ lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, 
     double *result = scratch + kEnergyBlocks * 8;
     // Every slot read below is written earlier in the same call, so nothing left over from a
     // previous call is used and nothing needs clearing.
-    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[0], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
+    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
                            result, s),
              "energy launch");
     double r[8];

@@ -170,6 +170,30 @@ constexpr int kEnergyThreads = 256;
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
                           const lf2_params &p, double *partials, double *result, cudaStream_t s);
 
+// Temporal blocking: `depth` fused steps per pass over x-y tiles of tile_x x tile_y output
+// sites (plus a depth-site halo), z-chunks of `zchunk` planes.  Unlike the one-step kernels it
+// reads phi, pi and the compensation from the front buffers and writes all three to the back
+// buffers, because neighbouring tiles read each other's halo columns of pi and comp too.
+struct TbArgs {
+    const void *phi;
+    void *phi_out;
+    const void *pi;
+    void *pi_out;
+    const float *comp;  // F32_KAHAN only
+    float *comp_out;
+    Geom g;
+    int ncomp;
+    lf2_precision prec;
+    lf2_params p;
+    double dt;
+};
+struct TbConfig {
+    int depth, cx, tile_x, tile_y, zchunk;
+};
+// Shape/configuration check; fills defaults for zero fields of `c`.
+bool tblock_supported(const TbArgs &a, TbConfig &c);
+cudaError_t launch_tblock(const TbArgs &a, const TbConfig &c, cudaStream_t s);
+
 // Fixed-size scratch of lf2_energy_noalloc: kEnergyBlocks*8 partials + 8 results (39 KB).
 constexpr int kEnergyNoallocDoubles = kEnergyBlocks * 8 + 8;
 cudaError_t energy_noalloc_scratch(double **out);

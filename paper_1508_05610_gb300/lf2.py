@@ -38,7 +38,8 @@ class lf2_energy_t(ctypes.Structure):
 
 
 class lf2_step_config(ctypes.Structure):
-    _fields_ = [("kernel", ctypes.c_int), ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int), ("depth", ctypes.c_int)]
+    _fields_ = [("kernel", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int),
+                ("depth", ctypes.c_int), ("cx", ctypes.c_int)]
 
 
 class LF2Error(RuntimeError):
@@ -179,8 +180,8 @@ def lf2_leapfrog(phi, pi, p: lf2_params, nsteps, stream=None):
 
 
 def lf2_leapfrog_ex(phi, pi, p: lf2_params, nsteps, kernel=LF2_KERNEL_AUTO, tile_y=0, zchunk=0, depth=0,
-                    stream=None):
-    cfg = lf2_step_config(kernel, tile_y, zchunk, depth)
+                    stream=None, tile_x=0, cx=0):
+    cfg = lf2_step_config(kernel, tile_x, tile_y, zchunk, depth, cx)
     _call("lf2_leapfrog_ex", phi, pi, ctypes.byref(p), int(nsteps), ctypes.byref(cfg), _stream_ptr(stream))
 
 

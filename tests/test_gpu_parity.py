@@ -35,7 +35,7 @@ def relmax(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def run_gpu(lf2, phi0, pi0, steps, prec, kw, half_kick=True, kernel=None, tile_y=0, zchunk=0):
+def run_gpu(lf2, phi0, pi0, steps, prec, kw, half_kick=True, kernel=None, tile_y=0, zchunk=0, **tb):
     nz, ny, nx, c = phi0.shape
     p = lf2.params(**kw)
     with lf2.System((nx, ny, nz), c, prec) as s:
@@ -45,7 +45,7 @@ def run_gpu(lf2, phi0, pi0, steps, prec, kw, half_kick=True, kernel=None, tile_y
         if kernel is None:
             lf2.lf2_leapfrog(s.phi, s.pi, p, steps)
         else:
-            lf2.lf2_leapfrog_ex(s.phi, s.pi, p, steps, kernel=kernel, tile_y=tile_y, zchunk=zchunk)
+            lf2.lf2_leapfrog_ex(s.phi, s.pi, p, steps, kernel=kernel, tile_y=tile_y, zchunk=zchunk, **tb)
         e = lf2.lf2_energy(s.phi, s.pi, p, ncomp=c)
         phi, pi = s.download()
     return phi, pi, e
@@ -169,3 +169,48 @@ def test_fp32_kahan_beats_plain_over_many_small_steps(lf2, ora):
     ek = relmax(run_gpu(lf2, phi0, pi0, steps, "f32k", kw)[0], ophi)
     ep = relmax(run_gpu(lf2, phi0, pi0, steps, "f32", kw)[0], ophi)
     assert ek <= 2.4e-7 and ek < ep / 10, (ek, ep)
+
+
+# ------------------------------------------------ temporal blocking: same bits as one step
+TB_SHAPES = [((64, 16, 12), 1), ((32, 16, 10), 2), ((96, 8, 9), 1), ((40, 24, 7), 2), ((20, 6, 5), 1)]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32k", "f32"])
+@pytest.mark.parametrize("shape,ncomp", TB_SHAPES)
+def test_tblock_bitwise_identical_to_single_steps(lf2, prec, shape, ncomp):
+    """Every depth, column width, tile and z-chunk (ragged tiles and chunks, lattices smaller
+    than the halo, step counts that leave a remainder) reproduces the one-step kernel bit for bit."""
+    nx, ny, nz = shape
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.01)
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.5, seed=17)
+    pi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=18)
+    steps = 11
+    ref = run_gpu(lf2, phi0, pi0, steps, prec, kw, kernel=lf2.LF2_KERNEL_SITE)
+    ran = 0
+    for depth in (2, 3, 4, 6, 8):
+        for cx in (1, 2):
+            for tile_x, tile_y in ((8, 4), (16, 8), (32, 16), (12, 6)):
+                for zchunk in (0, 5):
+                    try:
+                        got = run_gpu(lf2, phi0, pi0, steps, prec, kw, kernel=lf2.LF2_KERNEL_TBLOCK, depth=depth, cx=cx,
+                                      tile_x=tile_x, tile_y=tile_y, zchunk=zchunk)
+                    except lf2.LF2Error as e:
+                        assert e.status == lf2.LF2_ERR_UNSUPPORTED, e
+                        continue
+                    ran += 1
+                    cfg = (depth, cx, tile_x, tile_y, zchunk)
+                    assert np.array_equal(got[0], ref[0]), cfg
+                    assert np.array_equal(got[1], ref[1]), cfg
+                    assert got[2]["total"] == ref[2]["total"], cfg
+    assert ran >= 20
+
+
+def test_tblock_fp64_parity_with_oracle(lf2, ora):
+    nx, ny, nz = 48, 20, 13
+    kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)
+    phi0 = inputs.gaussian_field(nx, ny, nz, 2, sigma=0.3, seed=201)
+    pi0 = inputs.gaussian_field(nx, ny, nz, 2, sigma=0.1, seed=202)
+    ophi, opi = ora.evolve(phi0, pi0, 10, half_kick=True, **kw)
+    phi, pi, _ = run_gpu(lf2, phi0, pi0, 10, "f64", kw, kernel=lf2.LF2_KERNEL_TBLOCK, depth=4, cx=1, tile_x=16,
+                         tile_y=8)
+    assert relmax(phi, ophi) <= F64_TOL and relmax(pi, opi) <= F64_TOL
