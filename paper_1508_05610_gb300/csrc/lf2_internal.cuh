@@ -30,6 +30,7 @@ struct Coef64 {
 //   F_a = d_a * inv_dx2 - (lambda (s2 - eta^2) + m2) phi_a.
 struct Coef32 {
     float inv_dx2, lam, eta2, m2, dt;
+    float zero;  // always 0: a run-time zero for the packed path (see make_coef32x2)
 };
 
 // Energy (always FP64).
@@ -43,7 +44,7 @@ inline Coef64 make_coef64(const lf2_params &p, double dt) {
 }
 
 inline Coef32 make_coef32(const lf2_params &p, double dt) {
-    return Coef32{(float)(1.0 / (p.dx * p.dx)), (float)p.lambda, (float)(p.eta * p.eta), (float)p.m2, (float)dt};
+    return Coef32{(float)(1.0 / (p.dx * p.dx)), (float)p.lambda, (float)(p.eta * p.eta), (float)p.m2, (float)dt, 0.0f};
 }
 
 inline CoefE make_coefE(const lf2_params &p) {
@@ -130,6 +131,87 @@ __device__ __forceinline__ void kick_f32(const float (&c)[NC], const float (&xm)
     force_f32<NC>(c, xm, xp, ym, yp, zm, zp, F, k);
 #pragma unroll
     for (int a = 0; a < NC; ++a) p[a] = __fmaf_rn(k.dt, F[a], p[a]);
+}
+
+// ------------------------------------------------------- packed FP32 pairs (f32x2)
+// Two sites updated by one instruction stream with Blackwell's packed f32x2 arithmetic.
+// Each lane is an IEEE round-to-nearest FP32 operation, and the sequence below is the one of
+// force_f32 / update_f32 rewritten with exact sign identities of round-to-nearest
+// (RN(-a*b - c) = -RN(a*b + c)), so a packed update is bitwise equal to two scalar ones.
+// One caution, found by measurement: the assembler may fuse a packed multiply whose result
+// feeds a packed add or subtract into a single fused multiply-add (one rounding instead of
+// two) even with explicit .rn.  No product below feeds an add: c*c is formed as
+// fma(c, c, zero) with a zero the compiler cannot see (RN(c*c + 0) = RN(c*c) for every c),
+// and the other products feed the addend of an fma, which cannot be fused further.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void up2(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Coefficients broadcast to both lanes; n* are negated copies.
+struct Coef32x2 {
+    f32x2 inv_dx2, nlam, eta2, nm2, dt, ndt, zero;
+};
+
+// `zero` must be a run-time 0 (the caller passes a kernel argument), never a literal.
+__device__ __forceinline__ Coef32x2 make_coef32x2(const Coef32 &k, float zero) {
+    return Coef32x2{pk2(k.inv_dx2, k.inv_dx2), pk2(-k.lam, -k.lam), pk2(k.eta2, k.eta2), pk2(-k.m2, -k.m2),
+                    pk2(k.dt, k.dt),           pk2(-k.dt, -k.dt),   pk2(zero, zero)};
+}
+
+// update_f32 for two sites at once (lane 0 and lane 1 of every operand).
+template <int NC, bool KAHAN>
+__device__ __forceinline__ void update_f32x2(const f32x2 (&c)[NC], const f32x2 (&xm)[NC], const f32x2 (&xp)[NC],
+                                             const f32x2 (&ym)[NC], const f32x2 (&yp)[NC], const f32x2 (&zm)[NC],
+                                             const f32x2 (&zp)[NC], f32x2 (&p)[NC], f32x2 (&cmp)[NC],
+                                             f32x2 (&out)[NC], const Coef32x2 &k) {
+    f32x2 s2 = fma2(c[0], c[0], k.zero);
+#pragma unroll
+    for (int b = 1; b < NC; ++b) s2 = fma2(c[b], c[b], s2);
+    const f32x2 ng = fma2(k.nlam, sub2(s2, k.eta2), k.nm2);  // -g
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        const f32x2 dx_ = add2(sub2(xm[a], c[a]), sub2(xp[a], c[a]));
+        const f32x2 dy_ = add2(sub2(ym[a], c[a]), sub2(yp[a], c[a]));
+        const f32x2 dz_ = add2(sub2(zm[a], c[a]), sub2(zp[a], c[a]));
+        const f32x2 d = add2(add2(dx_, dy_), dz_);
+        const f32x2 F = fma2(d, k.inv_dx2, mul2(ng, c[a]));  // d/dx^2 - g c
+        p[a] = fma2(k.dt, F, p[a]);
+        if (KAHAN) {
+            const f32x2 ny = fma2(k.ndt, p[a], cmp[a]);  // -(dt p - comp)
+            const f32x2 t = sub2(c[a], ny);
+            cmp[a] = add2(sub2(t, c[a]), ny);
+            out[a] = t;
+        } else {
+            out[a] = fma2(k.dt, p[a], c[a]);
+        }
+    }
 }
 
 // ----------------------------------------------------------------- geometry helpers

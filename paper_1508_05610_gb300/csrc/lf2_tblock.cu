@@ -145,33 +145,65 @@ __device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__re
             left[a] = src[a - NC];
             right[a] = src[W + a];
         }
+        if constexpr (MODE != 3 && CX % 2 == 0) {
+            // FP32: two columns per packed f32x2 instruction stream
+            const Coef32x2 k2 = make_coef32x2(k, k.zero);
 #pragma unroll
-        for (int j = 0; j < CX; ++j) {
-            R c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], o[NC];
+            for (int m = 0; m < CX / 2; ++m) {
+                const int j0 = 2 * m, j1 = 2 * m + 1;
+                f32x2 c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], o[NC];
 #pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const int e = j * NC + a;
-                c[a] = st.lv[s - 1][1][e];
-                xm[a] = (j == 0) ? left[a] : st.lv[s - 1][1][e - NC];
-                xp[a] = (j == CX - 1) ? right[a] : st.lv[s - 1][1][e + NC];
-                ym[a] = dn[e];
-                yp[a] = up[e];
-                zm[a] = st.lv[s - 1][0][e];
-                zp[a] = st.lv[s - 1][2][e];
-                p[a] = st.pq[s][e];
-                cm[a] = (MODE == 1) ? (float)st.cq[s][e] : 0.0f;
+                for (int a = 0; a < NC; ++a) {
+                    const int e0 = j0 * NC + a, e1 = j1 * NC + a;
+                    const R *L = st.lv[s - 1][1];
+                    c[a] = pk2(L[e0], L[e1]);
+                    xm[a] = pk2((j0 == 0) ? left[a] : L[e0 - NC], L[e0]);
+                    xp[a] = pk2(L[e1], (j1 == CX - 1) ? right[a] : L[e1 + NC]);
+                    ym[a] = pk2(dn[e0], dn[e1]);
+                    yp[a] = pk2(up[e0], up[e1]);
+                    zm[a] = pk2(st.lv[s - 1][0][e0], st.lv[s - 1][0][e1]);
+                    zp[a] = pk2(st.lv[s - 1][2][e0], st.lv[s - 1][2][e1]);
+                    p[a] = pk2(st.pq[s][e0], st.pq[s][e1]);
+                    cm[a] = (MODE == 1) ? pk2(st.cq[s][e0], st.cq[s][e1]) : 0ull;
+                }
+                update_f32x2<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, o, k2);
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e0 = j0 * NC + a, e1 = j1 * NC + a;
+                    up2(o[a], out[e0], out[e1]);
+                    up2(p[a], st.pq[s][e0], st.pq[s][e1]);
+                    if (MODE == 1) up2(cm[a], st.cq[s][e0], st.cq[s][e1]);
+                }
             }
-            if constexpr (MODE == 3) {
-                update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, o, k);
-            } else {
-                update_f32<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, o, k);
-            }
+        } else {
 #pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const int e = j * NC + a;
-                out[e] = o[a];
-                st.pq[s][e] = p[a];
-                if (MODE == 1) st.cq[s][e] = cm[a];
+            for (int j = 0; j < CX; ++j) {
+                R c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], o[NC];
+    #pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e = j * NC + a;
+                    c[a] = st.lv[s - 1][1][e];
+                    xm[a] = (j == 0) ? left[a] : st.lv[s - 1][1][e - NC];
+                    xp[a] = (j == CX - 1) ? right[a] : st.lv[s - 1][1][e + NC];
+                    ym[a] = dn[e];
+                    yp[a] = up[e];
+                    zm[a] = st.lv[s - 1][0][e];
+                    zp[a] = st.lv[s - 1][2][e];
+                    p[a] = st.pq[s][e];
+                    cm[a] = (MODE == 1) ? (float)st.cq[s][e] : 0.0f;
+                }
+                if constexpr (MODE == 3) {
+                    update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, o, k);
+                } else {
+                    update_f32<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, o, k);
+                }
+    #pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e = j * NC + a;
+                    out[e] = o[a];
+                    st.pq[s][e] = p[a];
+                    if (MODE == 1) st.cq[s][e] = cm[a];
+                }
             }
         }
         if (s < T) {

@@ -175,13 +175,17 @@ def test_fp32_kahan_beats_plain_over_many_small_steps(lf2, ora):
 TB_SHAPES = [((64, 16, 12), 1), ((32, 16, 10), 2), ((96, 8, 9), 1), ((40, 24, 7), 2), ((20, 6, 5), 1)]
 
 
+TB_PARAMS = [dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.01), dict(dx=0.7, dt=0.03, lam=0.6, eta=1.3, m2=0.0)]
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32k", "f32"])
 @pytest.mark.parametrize("shape,ncomp", TB_SHAPES)
-def test_tblock_bitwise_identical_to_single_steps(lf2, prec, shape, ncomp):
+@pytest.mark.parametrize("pset", [0, 1])
+def test_tblock_bitwise_identical_to_single_steps(lf2, prec, shape, ncomp, pset):
     """Every depth, column width, tile and z-chunk (ragged tiles and chunks, lattices smaller
     than the halo, step counts that leave a remainder) reproduces the one-step kernel bit for bit."""
     nx, ny, nz = shape
-    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.01)
+    kw = TB_PARAMS[pset]
     phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.5, seed=17)
     pi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=18)
     steps = 11
