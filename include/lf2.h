@@ -197,6 +197,58 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
  * are those of lf2_energy; the result is copied into *out. */
 lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream);
 
+/* -------------------------------------------------------------------- ensembles */
+
+/* Groups n >= 1 independent (phi, pi) pairs -- one precision and component count, any
+ * lattice sizes, per-member parameters -- into a batched ensemble.  The paper runs many
+ * independent fields only as separate programs; here they share every kernel launch.
+ * Allocates the members' back buffers (temporal blocking needs them) and device tables.
+ * The fields must stay alive and must not be used by another ensemble until
+ * lf2_ensemble_destroy; their lattices cannot be destroyed meanwhile (LF2_ERR_STATE). */
+lf2_status lf2_ensemble_create(int n, const lf2_field *phis, const lf2_field *pis, const lf2_params *per_lattice,
+                               lf2_ensemble *out);
+
+/* Advances every member by nsteps (each member's phi_n / pi_{n-1/2} convention as in
+ * lf2_leapfrog) with ONE CUDA-graph launch on `stream`: nsteps/depth temporal-blocking passes,
+ * each a persistent kernel over a work list of (member, tile, z-chunk) items ordered longest
+ * first, then the leftover single steps.  The graph is captured on first use for a given
+ * nsteps and buffer state (this first call must not itself be inside a stream capture) and
+ * relaunched afterwards.  Results are bitwise those of running each member alone. */
+lf2_status lf2_ensemble_run(lf2_ensemble e, int nsteps, void *stream);
+
+/* Chooses the ensemble's pass configuration (depth, cx, tile) by timing candidates on a
+ * clone of the ensemble (members untouched); allocates the clone; synchronises `stream`. */
+lf2_status lf2_ensemble_tune(lf2_ensemble e, int flags, lf2_step_config *chosen, void *stream);
+
+/* Sets the pass configuration explicitly (kernel LF2_KERNEL_TBLOCK with depth/cx/tile_x/
+ * tile_y, or any other kernel for one-step passes).  LF2_ERR_UNSUPPORTED if it does not fit
+ * every member. */
+lf2_status lf2_ensemble_set_config(lf2_ensemble e, const lf2_step_config *c);
+
+/* Frees the ensemble's graphs and tables (not the member fields). */
+lf2_status lf2_ensemble_destroy(lf2_ensemble e);
+
+/* -------------------------------------------------------------------- autotuner */
+
+/* lf2_tune flags */
+#define LF2_TUNE_FORCE 1    /* re-tune even if a plan for this shape is cached */
+#define LF2_TUNE_ONE_STEP 2 /* only one-step kernels (no temporal blocking) */
+
+/* Picks the fastest kernel configuration for phi's lattice shape, component count and
+ * precision by timing candidates (one-step streaming tiles; temporal blocking of depth 2-8
+ * with several tiles and column widths) on a proxy lattice of the same x-y plane and at most
+ * 256 z-planes, filled with a copy of the fields' first planes -- phi and pi are not modified.
+ * The plan is cached per process (and appended to the file named by the environment variable
+ * LF2_TUNE_CACHE, which is read on first use) and used by every later lf2_leapfrog on a lattice
+ * of that shape.  Results do not depend on the plan: all variants are bitwise identical.
+ * Allocates the proxy fields and synchronises `stream`; call it before any stream capture.
+ * *chosen (may be NULL) receives the plan. */
+lf2_status lf2_tune(lf2_field phi, lf2_field pi, const lf2_params *p, int flags, lf2_step_config *chosen,
+                    void *stream);
+
+/* The cached plan for sizes[3] / ncomp / prec; LF2_ERR_STATE if none was tuned. */
+lf2_status lf2_tune_lookup(const int *sizes, int ncomp, lf2_precision prec, lf2_step_config *out);
+
 /* ------------------------------------------------------------------- utilities */
 
 const char *lf2_status_string(lf2_status s);

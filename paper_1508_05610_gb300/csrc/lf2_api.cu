@@ -6,7 +6,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -20,29 +19,7 @@
 
 using namespace lf2;
 
-struct lf2_lattice_s {
-    int dim;
-    int n[3];
-    int halo;
-    long long sites;
-    std::atomic<int> users{0};  // fields and ensembles still attached
-};
-
-struct lf2_field_s {
-    lf2_lattice lat = nullptr;
-    int ncomp = 0;
-    lf2_precision prec = LF2_F64;
-    size_t esize = 0;  // bytes per stored element
-    long long count = 0;  // sites * ncomp
-    void *val[2] = {nullptr, nullptr};  // value buffers; val[front] is current
-    bool own_val[2] = {false, false};
-    int front = 0;
-    float *comp[2] = {nullptr, nullptr};  // Kahan compensation of phi (F32_KAHAN); comp[cfront] current
-    bool own_comp[2] = {false, false};
-    int cfront = 0;
-    double *energy_scratch = nullptr;  // kEnergyBlocks*8 partials + 8 results (device)
-    double *energy_host = nullptr;     // 8 pinned doubles
-};
+#include "lf2_handles.h"
 
 namespace {
 
@@ -74,7 +51,6 @@ size_t elem_size(lf2_precision p) { return p == LF2_F64 ? sizeof(double) : sizeo
 
 bool valid_prec(int p) { return p == LF2_F64 || p == LF2_F32_KAHAN || p == LF2_F32; }
 
-Geom geom_of(const lf2_lattice_s *lat) { return Geom{lat->n[0], lat->n[1], lat->n[2], lat->sites}; }
 
 lf2_status check_params(const lf2_params *p) {
     if (!p) return fail(LF2_ERR_INVALID, "params is NULL");
@@ -92,6 +68,28 @@ lf2_status check_pair(lf2_field phi, lf2_field pi) {
     if (phi->prec != pi->prec) return fail(LF2_ERR_INVALID, "phi and pi have different precision");
     return LF2_OK;
 }
+
+lf2_status new_field(lf2_lattice lat, int ncomp, int prec, lf2_field *out) {
+    if (!lat || !out) return fail(LF2_ERR_INVALID, "lattice or output pointer is NULL");
+    if (!valid_prec(prec)) return fail(LF2_ERR_INVALID, "unknown precision %d", prec);
+    if (ncomp < 1) return fail(LF2_ERR_INVALID, "ncomp must be >= 1");
+    if (ncomp > kMaxComp) return fail(LF2_ERR_UNSUPPORTED, "ncomp %d not built (1 or 2)", ncomp);
+    return LF2_OK;
+}
+
+}  // namespace
+
+namespace lf2 {
+lf2_status set_error(lf2_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+lf2_status cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
 
 bool fault_injected(const char *what) {
     const char *f = getenv("LF2_FAULT");
@@ -181,15 +179,7 @@ TbArgs tb_args(lf2_field phi, lf2_field pi, const lf2_params *p) {
     return a;
 }
 
-lf2_status new_field(lf2_lattice lat, int ncomp, int prec, lf2_field *out) {
-    if (!lat || !out) return fail(LF2_ERR_INVALID, "lattice or output pointer is NULL");
-    if (!valid_prec(prec)) return fail(LF2_ERR_INVALID, "unknown precision %d", prec);
-    if (ncomp < 1) return fail(LF2_ERR_INVALID, "ncomp must be >= 1");
-    if (ncomp > kMaxComp) return fail(LF2_ERR_UNSUPPORTED, "ncomp %d not built (1 or 2)", ncomp);
-    return LF2_OK;
-}
-
-}  // namespace
+}  // namespace lf2
 
 extern "C" {
 
@@ -419,6 +409,11 @@ lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int
     cudaStream_t s = (cudaStream_t)stream;
     int kernel = cfg ? cfg->kernel : LF2_KERNEL_AUTO;
     if (kernel < LF2_KERNEL_AUTO || kernel > LF2_KERNEL_TBLOCK) return fail(LF2_ERR_INVALID, "unknown kernel %d", kernel);
+    lf2_step_config tuned{};
+    if (kernel == LF2_KERNEL_AUTO && plan_lookup(phi->lat->n, phi->ncomp, phi->prec, &tuned)) {
+        cfg = &tuned;
+        kernel = tuned.kernel;
+    }
     const int tile_y = cfg ? cfg->tile_y : 0;
     const int zchunk = cfg ? cfg->zchunk : 0;
     st = (kernel == LF2_KERNEL_TBLOCK) ? ensure_tblock(phi, pi, s) : ensure_dynamic(phi, s);

@@ -272,6 +272,29 @@ struct TbArgs {
 struct TbConfig {
     int depth, cx, tile_x, tile_y, zchunk;
 };
+// One member lattice of an ensemble pass (device table entry).  Buffer f ^ 1 is written
+// when buffer f = front ^ flip is read.
+struct TbMember {
+    const void *phi[2];
+    const void *pi[2];
+    const float *comp[2];
+    Geom g;
+    Coef32 k32;
+    Coef64 k64;
+    int zchunk;
+    int front;
+};
+struct TbEnsembleLaunch {
+    const TbMember *members;  // device
+    const int4 *items;        // device: (member, tile x, tile y, z-chunk), longest chunks first
+    int nitems;
+    int flip;
+    TbConfig c;
+    int ncomp;
+    lf2_precision prec;
+};
+cudaError_t launch_tblock_ensemble(const TbEnsembleLaunch &e, cudaStream_t s);
+
 // Shape/configuration check; fills defaults for zero fields of `c`.
 bool tblock_supported(const TbArgs &a, TbConfig &c);
 cudaError_t launch_tblock(const TbArgs &a, const TbConfig &c, cudaStream_t s);

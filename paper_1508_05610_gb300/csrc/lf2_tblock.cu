@@ -230,11 +230,12 @@ constexpr int tb_min_blocks() {
     return (T <= 4 && CX * NC * sizeof(R) <= 8) ? 2 : 1;
 }
 
+// One tile x z-chunk of a temporal-blocking pass: (bx, by) is the tile, bz the chunk.
 template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
-__global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>())) k_tblock(const R *__restrict__ phi, R *__restrict__ phi_out,
-                                                         const R *__restrict__ pi, R *__restrict__ pi_out,
-                                                         const float *__restrict__ comp, float *__restrict__ comp_out,
-                                                         Geom g, CoefT k, int TX, int TY, int zchunk) {
+__device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restrict__ phi_out, const R *__restrict__ pi,
+                                         R *__restrict__ pi_out, const float *__restrict__ comp,
+                                         float *__restrict__ comp_out, const Geom &g, const CoefT &k, int TX, int TY,
+                                         int zchunk, int bx, int by, int bz) {
     constexpr int TP = ((T + CX - 1) / CX) * CX;  // x halo, rounded to whole thread groups
     constexpr int W = CX * NC;                     // elements per thread per plane
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -246,8 +247,8 @@ __global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>())
     const int t = threadIdx.x;
     const int tx = t % RXT, ry = t / RXT;
     const int rx0 = tx * CX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zchunk;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int z0 = bz * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
 
     const int gx0 = wrap_any(x0 - TP + rx0, g.nx);
@@ -297,6 +298,38 @@ __global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>())
 }
 
 template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+__global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>()))
+    k_tblock(const R *__restrict__ phi, R *__restrict__ phi_out, const R *__restrict__ pi, R *__restrict__ pi_out,
+             const float *__restrict__ comp, float *__restrict__ comp_out, Geom g, CoefT k, int TX, int TY,
+             int zchunk) {
+    tb_block<R, NC, MODE, T, CX, CoefT>(phi, phi_out, pi, pi_out, comp, comp_out, g, k, TX, TY, zchunk, blockIdx.x,
+                                        blockIdx.y, blockIdx.z);
+}
+
+// Ensemble pass: one launch covers the tiles of every member lattice.  The blocks walk a
+// shared work list (longest chunks first) with a fixed stride, so the assignment is
+// deterministic; members are independent, so no block waits on another.
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+__global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>()))
+    k_tblock_ensemble(const TbMember *__restrict__ members, const int4 *__restrict__ items, int nitems, int flip,
+                      int TX, int TY) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const TbMember &m = members[w.x];
+        const int f = m.front ^ flip;
+        CoefT k;
+        if constexpr (MODE == 3)
+            k = m.k64;
+        else
+            k = m.k32;
+        tb_block<R, NC, MODE, T, CX, CoefT>((const R *)m.phi[f], (R *)m.phi[f ^ 1], (const R *)m.pi[f],
+                                            (R *)m.pi[f ^ 1], m.comp[f], const_cast<float *>(m.comp[f ^ 1]), m.g, k, TX, TY, m.zchunk,
+                                            w.y, w.z, w.w);
+        __syncthreads();
+    }
+}
+
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
 cudaError_t launch_t(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStream_t s) {
     constexpr int TP = ((T + CX - 1) / CX) * CX;
     const int RX = c.tile_x + 2 * TP, RY = c.tile_y + 2 * T;
@@ -310,6 +343,60 @@ cudaError_t launch_t(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStr
     kern<<<grid, threads, smem, s>>>((const R *)a.phi, (R *)a.phi_out, (const R *)a.pi, (R *)a.pi_out, a.comp,
                                      a.comp_out, a.g, k, c.tile_x, c.tile_y, c.zchunk);
     return cudaGetLastError();
+}
+
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+cudaError_t launch_ens_t(const TbEnsembleLaunch &e, cudaStream_t s) {
+    constexpr int TP = ((T + CX - 1) / CX) * CX;
+    const int RX = e.c.tile_x + 2 * TP, RY = e.c.tile_y + 2 * T;
+    const int threads = (RX / CX) * RY;
+    const size_t smem = (size_t)2 * T * (RY + 2) * RX * NC * sizeof(R);
+    auto kern = k_tblock_ensemble<R, NC, MODE, T, CX, CoefT>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (err != cudaSuccess) return err;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = (per_sm > 0 ? per_sm : 1) * sms;
+    if (grid > e.nitems) grid = e.nitems;
+    if (grid < 1) return cudaSuccess;
+    kern<<<grid, threads, smem, s>>>(e.members, e.items, e.nitems, e.flip, e.c.tile_x, e.c.tile_y);
+    return cudaGetLastError();
+}
+
+template <int T, int CX>
+cudaError_t launch_ens_depth(const TbEnsembleLaunch &e, cudaStream_t s) {
+    if (e.prec == LF2_F64) {
+        if constexpr (CX == 1)
+            return e.ncomp == 1 ? launch_ens_t<double, 1, 3, T, 1, Coef64>(e, s) : launch_ens_t<double, 2, 3, T, 1, Coef64>(e, s);
+        else if constexpr (CX == 2)
+            return e.ncomp == 1 ? launch_ens_t<double, 1, 3, T, 2, Coef64>(e, s) : cudaErrorNotSupported;
+        else
+            return cudaErrorNotSupported;
+    }
+    if constexpr (CX == 4) {
+        if (e.ncomp != 1) return cudaErrorNotSupported;
+        return e.prec == LF2_F32_KAHAN ? launch_ens_t<float, 1, 1, T, 4, Coef32>(e, s) : launch_ens_t<float, 1, 0, T, 4, Coef32>(e, s);
+    } else {
+        if (e.prec == LF2_F32_KAHAN)
+            return e.ncomp == 1 ? launch_ens_t<float, 1, 1, T, CX, Coef32>(e, s) : launch_ens_t<float, 2, 1, T, CX, Coef32>(e, s);
+        return e.ncomp == 1 ? launch_ens_t<float, 1, 0, T, CX, Coef32>(e, s) : launch_ens_t<float, 2, 0, T, CX, Coef32>(e, s);
+    }
+}
+
+template <int CX>
+cudaError_t launch_ens_cx(const TbEnsembleLaunch &e, cudaStream_t s) {
+    switch (e.c.depth) {
+        case 2: return launch_ens_depth<2, CX>(e, s);
+        case 3: return launch_ens_depth<3, CX>(e, s);
+        case 4: return launch_ens_depth<4, CX>(e, s);
+        case 6: return launch_ens_depth<6, CX>(e, s);
+        case 8: return launch_ens_depth<8, CX>(e, s);
+        default: return cudaErrorNotSupported;
+    }
 }
 
 template <int T, int CX>
@@ -393,6 +480,12 @@ bool tblock_supported(const TbArgs &a, TbConfig &c) {
         return false;
     if (a.prec == LF2_F32_KAHAN && (!a.comp || !a.comp_out)) return false;
     return true;
+}
+
+cudaError_t launch_tblock_ensemble(const TbEnsembleLaunch &e, cudaStream_t s) {
+    if (e.nitems == 0) return cudaSuccess;
+    if (e.c.cx == 4) return launch_ens_cx<4>(e, s);
+    return e.c.cx == 1 ? launch_ens_cx<1>(e, s) : launch_ens_cx<2>(e, s);
 }
 
 cudaError_t launch_tblock(const TbArgs &a, const TbConfig &c, cudaStream_t s) {

@@ -72,6 +72,14 @@ SIGNATURES = {
     "lf2_leapfrog_ex": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, ctypes.POINTER(lf2_step_config), _vp],
     "lf2_energy": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
     "lf2_energy_noalloc": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
+    "lf2_ensemble_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(lf2_params),
+                            ctypes.POINTER(_vp)],
+    "lf2_ensemble_run": [_vp, ctypes.c_int, _vp],
+    "lf2_ensemble_tune": [_vp, ctypes.c_int, ctypes.POINTER(lf2_step_config), _vp],
+    "lf2_ensemble_set_config": [_vp, ctypes.POINTER(lf2_step_config)],
+    "lf2_ensemble_destroy": [_vp],
+    "lf2_tune": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, ctypes.POINTER(lf2_step_config), _vp],
+    "lf2_tune_lookup": [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, ctypes.POINTER(lf2_step_config)],
     "lf2_status_string": [ctypes.c_int],
     "lf2_last_error": [],
     "lf2_version": [],
@@ -196,6 +204,57 @@ def lf2_energy_noalloc(phi, pi, p: lf2_params, stream=None, ncomp=2) -> dict:
     e = lf2_energy_t()
     _call("lf2_energy_noalloc", phi, pi, ctypes.byref(p), ctypes.byref(e), _stream_ptr(stream))
     return e.as_dict(ncomp)
+
+
+LF2_TUNE_FORCE, LF2_TUNE_ONE_STEP = 1, 2
+
+
+def _cfg_dict(c):
+    return {"kernel": c.kernel, "tile_x": c.tile_x, "tile_y": c.tile_y, "zchunk": c.zchunk, "depth": c.depth,
+            "cx": c.cx}
+
+
+def lf2_tune(phi, pi, p: lf2_params, flags=0, stream=None) -> dict:
+    """Times kernel configurations on a proxy of phi's lattice; returns the chosen one."""
+    c = lf2_step_config()
+    _call("lf2_tune", phi, pi, ctypes.byref(p), int(flags), ctypes.byref(c), _stream_ptr(stream))
+    return _cfg_dict(c)
+
+
+def lf2_tune_lookup(sizes, ncomp, prec) -> dict:
+    arr = (ctypes.c_int * 3)(*sizes)
+    c = lf2_step_config()
+    _call("lf2_tune_lookup", arr, ncomp, prec, ctypes.byref(c))
+    return _cfg_dict(c)
+
+
+def lf2_ensemble_create(phis, pis, params_list):
+    n = len(phis)
+    a = (_vp * n)(*phis)
+    b = (_vp * n)(*pis)
+    c = (lf2_params * n)(*params_list)
+    out = _vp()
+    _call("lf2_ensemble_create", n, a, b, c, ctypes.byref(out))
+    return out
+
+
+def lf2_ensemble_run(e, nsteps, stream=None):
+    _call("lf2_ensemble_run", e, int(nsteps), _stream_ptr(stream))
+
+
+def lf2_ensemble_tune(e, flags=0, stream=None) -> dict:
+    c = lf2_step_config()
+    _call("lf2_ensemble_tune", e, int(flags), ctypes.byref(c), _stream_ptr(stream))
+    return _cfg_dict(c)
+
+
+def lf2_ensemble_set_config(e, kernel=LF2_KERNEL_TBLOCK, tile_x=0, tile_y=0, zchunk=0, depth=0, cx=0):
+    c = lf2_step_config(kernel, tile_x, tile_y, zchunk, depth, cx)
+    _call("lf2_ensemble_set_config", e, ctypes.byref(c))
+
+
+def lf2_ensemble_destroy(e):
+    _call("lf2_ensemble_destroy", e)
 
 
 def lf2_status_string(s):

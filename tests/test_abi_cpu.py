@@ -139,3 +139,26 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, fn)).read()
                 bad = re.search(r"(from\s+oracle|import\s+oracle|oracle\.|lf2_oracle|\bora_[a-z]+\()", text)
                 assert bad is None, (os.path.join(dirpath, fn), bad and bad.group(0))
+
+
+def test_ensemble_and_tune_argument_checks(lib):
+    lat = lib.lf2_lattice_create([8, 8, 8])
+    try:
+        a = lib.lf2_field_wrap(lat, 1, lib.LF2_F32_KAHAN, [0x1000])
+        b = lib.lf2_field_wrap(lat, 1, lib.LF2_F32_KAHAN, [0x2000])
+        c = lib.lf2_field_wrap(lat, 1, lib.LF2_F64, [0x3000])
+        p = lib.params()
+        for phis, pis in (([a], [a]), ([a], [c]), ([a, a], [b, b]), ([], [])):
+            with pytest.raises(lib.LF2Error) as e:
+                lib.lf2_ensemble_create(phis, pis, [p] * len(phis))
+            assert e.value.status == lib.LF2_ERR_INVALID
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_ensemble_create([a], [b], [lib.params(dx=-1.0)])
+        assert e.value.status == lib.LF2_ERR_INVALID
+        with pytest.raises(lib.LF2Error) as e:
+            lib.lf2_tune_lookup((8, 8, 8), 1, lib.LF2_F32_KAHAN)
+        assert e.value.status == lib.LF2_ERR_STATE
+        for f in (a, b, c):
+            lib.lf2_field_free(f)
+    finally:
+        lib.lf2_lattice_destroy(lat)

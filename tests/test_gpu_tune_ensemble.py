@@ -1,0 +1,140 @@
+"""GPU tests of the autotuner and of batched ensembles.
+
+Both rest on one invariant: every kernel configuration computes bitwise the same result, so
+a tuned plan or a batched run must reproduce the one-thread-per-site kernel exactly."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_1508_05610_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lf2():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1508_05610_gb300 import build, lf2 as binding
+    build.build()
+    binding.load()
+    return binding
+
+
+def run_site(lf2, shape, ncomp, prec, phi0, pi0, kw, steps):
+    p = lf2.params(**kw)
+    with lf2.System(shape, ncomp, prec) as s:
+        s.upload(phi0, pi0)
+        lf2.lf2_leapfrog_ex(s.phi, s.pi, p, steps, kernel=lf2.LF2_KERNEL_SITE)
+        return s.download()
+
+
+@pytest.mark.parametrize("prec,ncomp", [("f32k", 1), ("f32", 2), ("f64", 1)])
+def test_tune_leaves_fields_untouched_and_plan_is_bitwise(lf2, prec, ncomp):
+    shape = (64, 48, 40)
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(*shape, ncomp, sigma=0.4, seed=61)
+    pi0 = inputs.gaussian_field(*shape, ncomp, sigma=0.1, seed=62)
+    p = lf2.params(**kw)
+    ref = run_site(lf2, shape, ncomp, prec, phi0, pi0, kw, 13)
+    with lf2.System(shape, ncomp, prec) as s:
+        s.upload(phi0, pi0)
+        before = s.download()
+        plan = lf2.lf2_tune(s.phi, s.pi, p, flags=lf2.LF2_TUNE_FORCE)
+        after = s.download()
+        assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+        assert plan == lf2.lf2_tune_lookup(shape, ncomp, lf2.PRECISIONS[prec])
+        lf2.lf2_leapfrog(s.phi, s.pi, p, 13)  # uses the tuned plan
+        got = s.download()
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), plan
+
+
+def test_tune_cache_file_is_read_by_a_fresh_process(lf2, tmp_path):
+    cache = tmp_path / "plans.txt"
+    code = r"""
+import sys, json
+sys.path.insert(0, %r)
+from paper_1508_05610_gb300 import lf2
+lf2.load()
+shape = (32, 32, 16)
+if sys.argv[1] == "tune":
+    s = lf2.System(shape, 1, "f32k")
+    print(json.dumps(lf2.lf2_tune(s.phi, s.pi, lf2.params(dt=0.05))))
+    s.close()
+else:
+    print(json.dumps(lf2.lf2_tune_lookup(shape, 1, lf2.LF2_F32_KAHAN)))
+""" % ROOT
+    env = dict(os.environ, LF2_TUNE_CACHE=str(cache))
+    a = subprocess.run([sys.executable, "-c", code, "tune"], env=env, capture_output=True, text=True, check=True)
+    b = subprocess.run([sys.executable, "-c", code, "lookup"], env=env, capture_output=True, text=True, check=True)
+    assert a.stdout.strip() == b.stdout.strip() and cache.exists()
+
+
+ENSEMBLE = [((24, 16, 12), 0.7), ((32, 32, 32), 1.3), ((40, 24, 20), 0.55), ((16, 16, 16), 1.9), ((64, 8, 28), 1.0)]
+
+
+@pytest.mark.parametrize("prec,ncomp", [("f32k", 1), ("f32k", 2), ("f64", 1)])
+def test_ensemble_members_equal_standalone_runs(lf2, prec, ncomp):
+    systems, refs, plist = [], [], []
+    try:
+        for i, (shape, lam) in enumerate(ENSEMBLE):
+            kw = dict(dx=1.0, dt=0.05, lam=lam, eta=1.0, m2=0.0)
+            phi0 = inputs.gaussian_field(*shape, ncomp, sigma=0.3, seed=100 + i)
+            pi0 = inputs.gaussian_field(*shape, ncomp, sigma=0.1, seed=200 + i)
+            refs.append((run_site(lf2, shape, ncomp, prec, phi0, pi0, kw, 11),
+                         run_site(lf2, shape, ncomp, prec, phi0, pi0, kw, 22)))
+            s = lf2.System(shape, ncomp, prec)
+            s.upload(phi0, pi0)
+            systems.append(s)
+            plist.append(lf2.params(**kw))
+        e = lf2.lf2_ensemble_create([s.phi for s in systems], [s.pi for s in systems], plist)
+        try:
+            lf2.lf2_ensemble_run(e, 11)  # 2 passes of depth 4 + 3 single steps
+            for s, (r11, _) in zip(systems, refs):
+                got = s.download()
+                assert np.array_equal(got[0], r11[0]) and np.array_equal(got[1], r11[1])
+            lf2.lf2_ensemble_run(e, 11)  # other buffer parity: a second captured graph
+            for s, (_, r22) in zip(systems, refs):
+                got = s.download()
+                assert np.array_equal(got[0], r22[0]) and np.array_equal(got[1], r22[1])
+        finally:
+            lf2.lf2_ensemble_destroy(e)
+    finally:
+        for s in systems:
+            s.close()
+
+
+def test_ensemble_tune_and_configs_bitwise(lf2):
+    prec, ncomp = "f32k", 1
+    systems, refs, plist = [], [], []
+    try:
+        for i, (shape, lam) in enumerate(ENSEMBLE):
+            kw = dict(dx=1.0, dt=0.05, lam=lam, eta=1.0, m2=0.0)
+            phi0 = inputs.gaussian_field(*shape, ncomp, sigma=0.3, seed=300 + i)
+            refs.append((phi0, run_site(lf2, shape, ncomp, prec, phi0, np.zeros_like(phi0), kw, 12)))
+            s = lf2.System(shape, ncomp, prec)
+            systems.append(s)
+            plist.append(lf2.params(**kw))
+        e = lf2.lf2_ensemble_create([s.phi for s in systems], [s.pi for s in systems], plist)
+        try:
+            chosen = lf2.lf2_ensemble_tune(e)
+            for cfg in (None, dict(depth=2, cx=1, tile_x=12, tile_y=8), dict(depth=3, cx=2, tile_x=24, tile_y=16),
+                        dict(kernel=lf2.LF2_KERNEL_STREAM)):
+                if cfg is not None:
+                    lf2.lf2_ensemble_set_config(e, **cfg)
+                for s, (phi0, _) in zip(systems, refs):
+                    s.upload(phi0, np.zeros_like(phi0))
+                lf2.lf2_ensemble_run(e, 12)
+                for s, (_, r) in zip(systems, refs):
+                    got = s.download()
+                    assert np.array_equal(got[0], r[0]) and np.array_equal(got[1], r[1]), (chosen, cfg)
+        finally:
+            lf2.lf2_ensemble_destroy(e)
+    finally:
+        for s in systems:
+            s.close()
