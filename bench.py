@@ -49,6 +49,13 @@ DP_INSTR_PER_SITE = {1: 10, 2: 19}
 CSRC = os.path.join(ROOT, "paper_1508_05610_gb300", "csrc")
 
 
+def traffic_key(prec, cfg):
+    if cfg.get("kernel") == 3:
+        return (f"k_tblock_{prec}_c{NCOMP}_{N}_d{cfg.get('depth')}_cx{cfg.get('cx')}_"
+                f"{cfg.get('tile_x')}x{cfg.get('tile_y')}")
+    return f"k_stream_{prec}_c{NCOMP}_{N}"
+
+
 def measured_traffic(key):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     import hashlib
@@ -129,25 +136,33 @@ class ClockSampler:
 
 # ------------------------------------------------------------------- GPU arm helpers
 class WrappedPair:
-    """phi and pi as torch device tensors, borrowed by the library through lf2_field_wrap."""
+    """phi and pi (and their back buffers) as torch device tensors, borrowed by the library
+    through lf2_field_wrap, so every buffer the kernels touch is visible as a tensor."""
 
     def __init__(self, torch, lf2, prec, phi0):
         self.torch, self.lf2, self.prec = torch, lf2, lf2.PRECISIONS[prec]
         dtype = torch.float64 if prec == "f64" else torch.float32
         self.phi = phi0.to(dtype=dtype, copy=True).contiguous()
-        self.back = torch.empty_like(self.phi)
-        self.pi = torch.zeros_like(self.phi)
-        ptrs = [self.phi.data_ptr(), self.back.data_ptr()]
+        self.tensors = [self.phi, torch.empty_like(self.phi)]
+        ptrs = [t.data_ptr() for t in self.tensors]
         if self.prec == lf2.LF2_F32_KAHAN:
-            self.comp = torch.zeros_like(self.phi)
-            ptrs.append(self.comp.data_ptr())
+            comp = [torch.zeros_like(self.phi), torch.zeros_like(self.phi)]
+            self.tensors += comp
+            ptrs += [t.data_ptr() for t in comp]
+        pis = [torch.zeros_like(self.phi), torch.empty_like(self.phi)]
+        self.tensors += pis
         self.lat = lf2.lf2_lattice_create((N, N, N))
         self.fphi = lf2.lf2_field_wrap(self.lat, NCOMP, self.prec, ptrs)
-        self.fpi = lf2.lf2_field_wrap(self.lat, NCOMP, self.prec, [self.pi.data_ptr()])
+        self.fpi = lf2.lf2_field_wrap(self.lat, NCOMP, self.prec, [t.data_ptr() for t in pis])
+
+    def _tensor(self, ptr):
+        return next(t for t in self.tensors if t.data_ptr() == ptr)
 
     def front(self):
-        ptr = self.lf2.lf2_field_buffer(self.fphi, 0)
-        return self.phi if ptr == self.phi.data_ptr() else self.back
+        return self._tensor(self.lf2.lf2_field_buffer(self.fphi, 0))
+
+    def pi_front(self):
+        return self._tensor(self.lf2.lf2_field_buffer(self.fpi, 0))
 
     def close(self):
         self.lf2.lf2_field_free(self.fphi)
@@ -155,19 +170,26 @@ class WrappedPair:
         self.lf2.lf2_lattice_destroy(self.lat)
 
 
-def time_steps(torch, lf2, pair, p, steps, warmup, stream):
-    """Warm-up, then EXACTLY `steps` leapfrog steps between CUDA events on the launch stream."""
+def time_steps(torch, lf2, pair, p, steps, warmup, stream, cfg):
+    """Warm-up, then EXACTLY `steps` leapfrog steps between CUDA events on the launch stream.
+    With a one-step kernel each step is one launch; with temporal blocking the steps go in
+    passes of `depth` (one launch each) plus single steps for the remainder."""
     lf2.lf2_leapfrog_init(pair.fphi, pair.fpi, p, stream)
+    depth = cfg.get("depth", 0) if cfg.get("kernel") == lf2.LF2_KERNEL_TBLOCK else 1
     for _ in range(warmup):
-        lf2.lf2_leapfrog(pair.fphi, pair.fpi, p, 1, stream)
+        lf2.lf2_leapfrog_ex(pair.fphi, pair.fpi, p, depth, stream=stream, **cfg)
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
-    for _ in range(steps):
-        lf2.lf2_leapfrog(pair.fphi, pair.fpi, p, 1, stream)
+    done = 0
+    while done < steps:
+        n = min(depth, steps - done)
+        lf2.lf2_leapfrog_ex(pair.fphi, pair.fpi, p, n, stream=stream, **cfg)
+        done += n
     stop.record(stream)
     torch.cuda.synchronize()
-    return start.elapsed_time(stop) / 1e3
+    launches = steps // depth + steps % depth
+    return start.elapsed_time(stop) / 1e3, launches
 
 
 def run_gpu(args):
@@ -204,13 +226,21 @@ def run_gpu(args):
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
         return float(x.item())
 
-    results = {}
+    # kernel configurations: FP64 on the plain one-step streaming kernel; FP32+Kahan tuned
+    # (the tuner times candidates on a copy of the lattice before the timed region)
+    cfgs = {"f64": {"kernel": lf2.LF2_KERNEL_STREAM}}
+    tune_pair = WrappedPair(torch, lf2, "f32k", phi0)
+    cfgs["f32k"] = {k: v for k, v in lf2.lf2_tune(tune_pair.fphi, tune_pair.fpi, p, stream=stream).items() if v}
+    tune_pair.close()
+    del tune_pair
+
+    results, launches = {}, {}
     with ClockSampler(local) as clocks:
         for prec in ("f64", "f32k"):
             pair = WrappedPair(torch, lf2, prec, phi0)
             barrier()
-            t = max_over_ranks(time_steps(torch, lf2, pair, p, args.steps, args.warmup, stream))
-            results[prec] = t
+            t, nl = time_steps(torch, lf2, pair, p, args.steps, args.warmup, stream, cfgs[prec])
+            results[prec], launches[prec] = max_over_ranks(t), nl
             pair.close()
             del pair
             torch.cuda.empty_cache()
@@ -224,12 +254,12 @@ def run_gpu(args):
         lf2.lf2_leapfrog_init(pairs[prec].fphi, pairs[prec].fpi, p, stream)
     for n in (10, 100):
         for prec in pairs:
-            lf2.lf2_leapfrog(pairs[prec].fphi, pairs[prec].fpi, p, n - done, stream)
+            lf2.lf2_leapfrog_ex(pairs[prec].fphi, pairs[prec].fpi, p, n - done, stream=stream, **cfgs[prec])
         done = n
         e64 = lf2.lf2_energy(pairs["f64"].fphi, pairs["f64"].fpi, p, stream)
         e32 = lf2.lf2_energy(pairs["f32k"].fphi, pairs["f32k"].fpi, p, stream)
         a, b = pairs["f32k"].front().double(), pairs["f64"].front()
-        pa, pb = pairs["f32k"].pi.double(), pairs["f64"].pi
+        pa, pb = pairs["f32k"].pi_front().double(), pairs["f64"].pi_front()
         err[str(n)] = {"phi_relmax": float((a - b).abs().max() / b.abs().max()),
                        "pi_relmax": float((pa - pb).abs().max() / pb.abs().max()),
                        "energy_rel": abs(e32["total"] - e64["total"]) / abs(e64["total"])}
@@ -275,15 +305,19 @@ def run_gpu(args):
         return sites * world * args.steps / t / 1e9
 
     def roof(prec, t, traffic_key):
-        per_launch = t / args.steps
-        achieved = BYTES_PER_SITE[prec] * sites / per_launch / 1e9
+        # one launch = one pass over HBM = `depth` steps; algorithmic bytes of a pass are the
+        # one-step compulsory bytes (read phi, pi, comp; write them once)
+        depth = cfgs[prec].get("depth", 1) if cfgs[prec].get("kernel") == lf2.LF2_KERNEL_TBLOCK else 1
+        per_step = t / args.steps
+        achieved = BYTES_PER_SITE[prec] * sites / (per_step * depth) / 1e9
         hbm = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                "frac": round(achieved / hbm_peak, 4), "traffic": measured_traffic(traffic_key),
                "peak_source": f"{peak_src} HBM copy bandwidth",
-               "bytes_per_site_update": BYTES_PER_SITE[prec]}
+               "bytes_per_site_update": BYTES_PER_SITE[prec], "steps_per_launch": depth,
+               "effective_frac": round(BYTES_PER_SITE[prec] * sites / per_step / 1e9 / hbm_peak, 4)}
         if prec != "f64":
             return hbm
-        ginst = DP_INSTR_PER_SITE[NCOMP] * sites / per_launch / 1e9
+        ginst = DP_INSTR_PER_SITE[NCOMP] * sites / per_step / 1e9
         return {"bound": "alu", "achieved": round(ginst, 1), "peak": round(FP64_PEAK_GINST, 1),
                 "unit": "G FP64 instr/s", "frac": round(ginst / FP64_PEAK_GINST, 4),
                 "traffic": hbm["traffic"], "peak_source": "nominal FP64 rate 1.25 TFLOP/s = 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
@@ -298,13 +332,15 @@ def run_gpu(args):
                    "ncomp": NCOMP, "sites": sites, "precision": "f64", "parallelism": f"replicas x{world}",
                    "l2_policy": "state 805 MB > 129 MB L2; no flush needed"},
         "roofline": roof("f64", t64, "k_stream_f64_c2_256"),
+        "kernel": "k_stream (one step per launch)",
         "fp32_kahan": {"value": round(gsu(t32), 3), "unit": UNIT, "ms_per_step": round(t32 / args.steps * 1e3, 5),
-                       "roofline": roof("f32k", t32, "k_stream_f32k_c2_256"), "speedup_vs_fp64": round(t64 / t32, 3),
+                       "roofline": roof("f32k", t32, traffic_key("f32k", cfgs["f32k"])),
+                       "plan": cfgs["f32k"], "launches": launches["f32k"], "speedup_vs_fp64": round(t64 / t32, 3),
                        "error_vs_fp64": err},
         "e2e": {"value": round(sites * world * args.steps / t_e2e / 1e9, 3), "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": (state_bytes + 64) / args.steps,
                 "note": "upload phi,pi from pinned host + half-kick + K steps + energy + download, per step"},
-        "gpu_launches": args.steps,
+        "gpu_launches": launches["f64"],
         "clocks": clk,
     }
     if args.cpu_baseline:

@@ -214,6 +214,34 @@ __device__ __forceinline__ void update_f32x2(const f32x2 (&c)[NC], const f32x2 (
     }
 }
 
+// update_f32 for one two-component site, its components packed as one f32x2 pair (the
+// interleaved storage order): |phi|^2 and the potential coefficient are formed in scalar
+// exactly as force_f32 does, everything per component runs packed.
+template <bool KAHAN>
+__device__ __forceinline__ void update_f32_site2(f32x2 c, f32x2 xm, f32x2 xp, f32x2 ym, f32x2 yp, f32x2 zm, f32x2 zp,
+                                                 f32x2 &p, f32x2 &cmp, f32x2 &out, const Coef32x2 &k,
+                                                 const Coef32 &ks) {
+    float c0, c1;
+    up2(c, c0, c1);
+    const float s2 = __fmaf_rn(c1, c1, __fmul_rn(c0, c0));
+    const float ngs = __fmaf_rn(-ks.lam, __fsub_rn(s2, ks.eta2), -ks.m2);  // -g
+    const f32x2 ng = pk2(ngs, ngs);
+    const f32x2 dx_ = add2(sub2(xm, c), sub2(xp, c));
+    const f32x2 dy_ = add2(sub2(ym, c), sub2(yp, c));
+    const f32x2 dz_ = add2(sub2(zm, c), sub2(zp, c));
+    const f32x2 d = add2(add2(dx_, dy_), dz_);
+    const f32x2 F = fma2(d, k.inv_dx2, mul2(ng, c));
+    p = fma2(k.dt, F, p);
+    if (KAHAN) {
+        const f32x2 ny = fma2(k.ndt, p, cmp);
+        const f32x2 t = sub2(c, ny);
+        cmp = add2(sub2(t, c), ny);
+        out = t;
+    } else {
+        out = fma2(k.dt, p, c);
+    }
+}
+
 // ----------------------------------------------------------------- geometry helpers
 struct Geom {
     int nx, ny, nz;

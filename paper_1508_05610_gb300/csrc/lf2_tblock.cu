@@ -145,7 +145,26 @@ __device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__re
             left[a] = src[a - NC];
             right[a] = src[W + a];
         }
-        if constexpr (MODE != 3 && CX % 2 == 0) {
+        if constexpr (MODE != 3 && NC == 2) {
+            // FP32 complex: the two components of a site form one f32x2 pair
+            const Coef32x2 k2 = make_coef32x2(k, k.zero);
+            const R *L = st.lv[s - 1][1];
+#pragma unroll
+            for (int j = 0; j < CX; ++j) {
+                const int e = 2 * j;
+                f32x2 p = pk2(st.pq[s][e], st.pq[s][e + 1]);
+                f32x2 cm = (MODE == 1) ? pk2(st.cq[s][e], st.cq[s][e + 1]) : 0ull;
+                f32x2 o;
+                update_f32_site2<MODE == 1>(
+                    pk2(L[e], L[e + 1]), (j == 0) ? pk2(left[0], left[1]) : pk2(L[e - 2], L[e - 1]),
+                    (j == CX - 1) ? pk2(right[0], right[1]) : pk2(L[e + 2], L[e + 3]), pk2(dn[e], dn[e + 1]),
+                    pk2(up[e], up[e + 1]), pk2(st.lv[s - 1][0][e], st.lv[s - 1][0][e + 1]),
+                    pk2(st.lv[s - 1][2][e], st.lv[s - 1][2][e + 1]), p, cm, o, k2, k);
+                up2(o, out[e], out[e + 1]);
+                up2(p, st.pq[s][e], st.pq[s][e + 1]);
+                if (MODE == 1) up2(cm, st.cq[s][e], st.cq[s][e + 1]);
+            }
+        } else if constexpr (MODE != 3 && CX % 2 == 0) {
             // FP32: two columns per packed f32x2 instruction stream
             const Coef32x2 k2 = make_coef32x2(k, k.zero);
 #pragma unroll

@@ -1,0 +1,77 @@
+"""Run one kernel configuration on one lattice and print its throughput (one JSON line).
+
+    python -m paper_1508_05610_gb300.runcase --n 256 --ncomp 2 --prec f32k \\
+        --kernel tblock --depth 3 --cx 1 --tile 10x24 --steps 24
+
+``--kernel tune`` lets lf2_tune choose.  The fields hold seeded Gaussian data generated on the
+device; the timed region is `--steps` steps between CUDA events after `--warmup` steps.
+Used to compare configurations and as the command line of the committed ncu summaries.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+KERNELS = {"auto": 0, "site": 1, "stream": 2, "tblock": 3}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, nargs="+", default=[256], help="side, or nx ny nz")
+    ap.add_argument("--ncomp", type=int, default=1)
+    ap.add_argument("--prec", default="f32k", choices=["f64", "f32k", "f32"])
+    ap.add_argument("--kernel", default="auto", choices=list(KERNELS) + ["tune"])
+    ap.add_argument("--depth", type=int, default=0)
+    ap.add_argument("--cx", type=int, default=0)
+    ap.add_argument("--tile", default="0x0", help="tile_x x tile_y (tile_y alone matters for stream)")
+    ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--warmup", type=int, default=2)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    from . import build, inputs, lf2
+    build.build()
+    lf2.load()
+    nx, ny, nz = (args.n * 3)[:3] if len(args.n) == 1 else args.n
+    stream = torch.cuda.current_stream()
+    p = lf2.params(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    tx, ty = (int(v) for v in args.tile.split("x"))
+    dtype = torch.float64 if args.prec == "f64" else torch.float32
+    prec = lf2.PRECISIONS[args.prec]
+    # every buffer the kernels use is a torch tensor borrowed through lf2_field_wrap
+    phi = inputs.gaussian_field_device(nx, ny, nz, args.ncomp, sigma=0.1, dtype=dtype)
+    bufs = [phi, torch.empty_like(phi)]
+    if prec == lf2.LF2_F32_KAHAN:
+        bufs += [torch.zeros_like(phi), torch.zeros_like(phi)]
+    pis = [torch.zeros_like(phi), torch.empty_like(phi)]
+    lat = lf2.lf2_lattice_create((nx, ny, nz))
+    fphi = lf2.lf2_field_wrap(lat, args.ncomp, prec, [t.data_ptr() for t in bufs])
+    fpi = lf2.lf2_field_wrap(lat, args.ncomp, prec, [t.data_ptr() for t in pis])
+    try:
+        lf2.lf2_leapfrog_init(fphi, fpi, p, stream)
+        if args.kernel == "tune":
+            cfg = {k: v for k, v in lf2.lf2_tune(fphi, fpi, p, stream=stream).items() if v}
+        else:
+            cfg = {"kernel": KERNELS[args.kernel], "depth": args.depth, "cx": args.cx, "tile_x": tx, "tile_y": ty,
+                   "zchunk": args.zchunk}
+        lf2.lf2_leapfrog_ex(fphi, fpi, p, args.warmup, stream=stream, **cfg)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lf2.lf2_leapfrog_ex(fphi, fpi, p, args.steps, stream=stream, **cfg)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+    finally:
+        lf2.lf2_field_free(fphi)
+        lf2.lf2_field_free(fpi)
+        lf2.lf2_lattice_destroy(lat)
+    sites = nx * ny * nz
+    print(json.dumps({"lattice": [nx, ny, nz], "ncomp": args.ncomp, "prec": args.prec, "config": cfg,
+                      "steps": args.steps, "seconds": t, "gsu_per_s": sites * args.steps / t / 1e9}))
+
+
+if __name__ == "__main__":
+    main()
