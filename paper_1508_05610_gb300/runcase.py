@@ -26,7 +26,7 @@ def main(argv=None):
     ap.add_argument("--tile", default="0x0", help="tile_x x tile_y (tile_y alone matters for stream)")
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--steps", type=int, default=24)
-    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=8)
     args = ap.parse_args(argv)
 
     import torch
