@@ -100,7 +100,7 @@ __device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__re
                                              int ps2, int row_e, const CoefT &k, bool load_next,
                                              const R *__restrict__ nphi, const R *__restrict__ npi,
                                              const float *__restrict__ ncomp, bool store, R *__restrict__ ophi,
-                                             R *__restrict__ opi, float *__restrict__ ocomp) {
+                                             R *__restrict__ opi, float *__restrict__ ocomp, bool shfl_x) {
     constexpr int W = CX * NC;
     R in_phi[W], in_pi[W], in_c[W];
 #pragma unroll
@@ -140,10 +140,21 @@ __device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__re
         R up[W], dn[W], left[NC], right[NC], out[W];
         vload_s<R, W>(src + row_e, up);
         vload_s<R, W>(src - row_e, dn);
+        if (shfl_x) {
+            // region rows are whole lane groups: the x-neighbours are the adjacent lanes' own
+            // columns (at a row's ends the values are from another row, but those columns are
+            // outside every stage's exact region and their results are never read)
 #pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            left[a] = src[a - NC];
-            right[a] = src[W + a];
+            for (int a = 0; a < NC; ++a) {
+                left[a] = __shfl_up_sync(0xffffffffu, st.lv[s - 1][1][(CX - 1) * NC + a], 1);
+                right[a] = __shfl_down_sync(0xffffffffu, st.lv[s - 1][1][a], 1);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                left[a] = src[a - NC];
+                right[a] = src[W + a];
+            }
         }
         if constexpr (MODE != 3 && NC == 2) {
             // FP32 complex: the two components of a site form one f32x2 pair
@@ -305,6 +316,9 @@ __device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restric
     // output plane of stage T in iteration i is i - T; stores start at i = z0 + T
     long long out_off = (long long)(z0 - 2 * T - 1) * planeE + colE;  // advanced before each use
     R *const base = sm + s_own;
+    // x-neighbours by warp shuffle when every region row is a whole group of lanes within one
+    // warp and the block is whole warps
+    const bool shfl_x = (32 % RXT == 0) && ((RXT * RY) % 32 == 0);
     for (int i = ibeg; i < iend; ++i) {
         pl = (pl + 1 == g.nz) ? 0 : pl + 1;
         const long long noff = (long long)pl * planeE + colE;
@@ -312,7 +326,7 @@ __device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restric
         const int par = i & 1;
         tb_iteration<R, NC, MODE, T, CX>(st, base + par * ps, base + (par ^ 1) * ps, 2 * ps, row_e, k, i + 1 < iend,
                                          phi + noff, pi + noff, comp + noff, out_col && i - T >= z0,
-                                         phi_out + out_off, pi_out + out_off, comp_out + out_off);
+                                         phi_out + out_off, pi_out + out_off, comp_out + out_off, shfl_x);
     }
 }
 

@@ -193,7 +193,7 @@ def test_tblock_bitwise_identical_to_single_steps(lf2, prec, shape, ncomp, pset)
     ran = 0
     for depth in (2, 3, 4, 6, 8):
         for cx in (1, 2):
-            for tile_x, tile_y in ((8, 4), (16, 8), (32, 16), (12, 6)):
+            for tile_x, tile_y in ((8, 4), (16, 8), (32, 16), (12, 6), (24, 8), (56, 8)):
                 for zchunk in (0, 5):
                     try:
                         got = run_gpu(lf2, phi0, pi0, steps, prec, kw, kernel=lf2.LF2_KERNEL_TBLOCK, depth=depth, cx=cx,
