@@ -237,7 +237,8 @@ lf2_status lf2_ensemble_destroy(lf2_ensemble e);
 /* Picks the fastest kernel configuration for phi's lattice shape, component count and
  * precision by timing candidates (one-step streaming tiles; temporal blocking of depth 2-8
  * with several tiles and column widths) on a proxy lattice of the same x-y plane and at most
- * 256 z-planes, filled with a copy of the fields' first planes -- phi and pi are not modified.
+ * 256 z-planes (fewer for very large planes, to stay within about 8 GB), filled with a copy
+ * of the fields' first planes -- phi and pi are not modified.
  * The plan is cached per process (and appended to the file named by the environment variable
  * LF2_TUNE_CACHE, which is read on first use) and used by every later lf2_leapfrog on a lattice
  * of that shape.  Results do not depend on the plan: all variants are bitwise identical.

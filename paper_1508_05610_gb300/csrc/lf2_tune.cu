@@ -22,7 +22,8 @@
 namespace lf2 {
 namespace {
 
-constexpr int kProxyPlanes = 256;
+constexpr int kProxyPlanes = 256;           // at most this many z-planes
+constexpr size_t kProxyBytes = 8ull << 30;  // and at most this much device memory
 constexpr int kTuneSteps = 24;  // divisible by every depth 2, 3, 4, 6, 8
 
 using Key = std::tuple<int, int, int, int, int, int>;  // nx, ny, nz, ncomp, prec, sm count
@@ -119,7 +120,10 @@ extern "C" lf2_status lf2_tune(lf2_field phi, lf2_field pi, const lf2_params *p,
     }
     cudaStream_t s = (cudaStream_t)stream;
     // proxy lattice: same x-y plane, first planes of the real fields
-    const int pz = n[2] < kProxyPlanes ? n[2] : kProxyPlanes;
+    // six buffers (phi, pi, compensation, each with a back buffer) of one plane
+    const size_t plane_bytes = (size_t)n[0] * n[1] * phi->ncomp * 4 * sizeof(float) * 2;
+    int pz = n[2] < kProxyPlanes ? n[2] : kProxyPlanes;
+    while (pz > 32 && (size_t)pz * plane_bytes > kProxyBytes) pz /= 2;
     const int psizes[3] = {n[0], n[1], pz};
     lf2_lattice plat = nullptr;
     lf2_field pphi = nullptr, ppi = nullptr;
