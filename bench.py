@@ -134,6 +134,34 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------------- multi-rank helpers
+def rank_info():
+    """(rank, world size, local rank) from the torchrun environment (1 process: 0, 1, 0)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(t, dist, device):
+    """Slowest rank's time: replicas are timed independently and the job takes the maximum."""
+    if dist is None:
+        return t
+    import torch
+    x = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def replica_seed(rank):
+    """Each replica evolves its own lattice: seeds differ per rank."""
+    from paper_1508_05610_gb300 import inputs
+    return inputs.BASE_SEED + rank
+
+
+def aggregate_gsu(sites, world, steps, seconds):
+    """Whole-job throughput: every rank's site-updates over the slowest rank's time."""
+    return sites * world * steps / seconds / 1e9
+
+
 # ------------------------------------------------------------------- GPU arm helpers
 class WrappedPair:
     """phi and pi (and their back buffers) as torch device tensors, borrowed by the library
@@ -197,9 +225,7 @@ def run_gpu(args):
 
     from paper_1508_05610_gb300 import build, inputs, lf2
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_info()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -212,19 +238,13 @@ def run_gpu(args):
     p = lf2.params(**KW)
     hbm_peak, peak_src = peaks()
 
-    phi0 = inputs.gaussian_field_device(N, N, N, NCOMP, sigma=0.1, seed=inputs.BASE_SEED + rank)
+    phi0 = inputs.gaussian_field_device(N, N, N, NCOMP, sigma=0.1, seed=replica_seed(rank))
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(t):
-        if dist is None:
-            return t
-        x = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        return float(x.item())
 
     # kernel configurations: FP64 on the plain one-step streaming kernel; FP32+Kahan tuned
     # (the tuner times candidates on a copy of the lattice before the timed region)
@@ -240,7 +260,7 @@ def run_gpu(args):
             pair = WrappedPair(torch, lf2, prec, phi0)
             barrier()
             t, nl = time_steps(torch, lf2, pair, p, args.steps, args.warmup, stream, cfgs[prec])
-            results[prec], launches[prec] = max_over_ranks(t), nl
+            results[prec], launches[prec] = max_over_ranks(t, dist, "cuda"), nl
             pair.close()
             del pair
             torch.cuda.empty_cache()
@@ -293,7 +313,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         e2e_once(args.steps)
         torch.cuda.synchronize()
-        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     state_bytes = N ** 3 * NCOMP * 8 * 2
 
     if rank != 0:
@@ -302,7 +322,7 @@ def run_gpu(args):
         return
 
     def gsu(t):
-        return sites * world * args.steps / t / 1e9
+        return aggregate_gsu(sites, world, args.steps, t)
 
     def roof(prec, t, traffic_key):
         # one launch = one pass over HBM = `depth` steps; algorithmic bytes of a pass are the
@@ -337,7 +357,7 @@ def run_gpu(args):
                        "roofline": roof("f32k", t32, traffic_key("f32k", cfgs["f32k"])),
                        "plan": cfgs["f32k"], "launches": launches["f32k"], "speedup_vs_fp64": round(t64 / t32, 3),
                        "error_vs_fp64": err},
-        "e2e": {"value": round(sites * world * args.steps / t_e2e / 1e9, 3), "unit": UNIT,
+        "e2e": {"value": round(aggregate_gsu(sites, world, args.steps, t_e2e), 3), "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": (state_bytes + 64) / args.steps,
                 "note": "upload phi,pi from pinned host + half-kick + K steps + energy + download, per step"},
         "gpu_launches": launches["f64"],
@@ -374,8 +394,8 @@ def cpu_baseline():
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    rank = rank_info()[0]
+    if rank != 0:  # the CPU reference runs once, on rank 0
         return
     threads = os.cpu_count() or 1
     nz_slab = 16

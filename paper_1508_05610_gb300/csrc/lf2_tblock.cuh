@@ -1,0 +1,438 @@
+#pragma once
+// lf2_tblock.cuh -- temporal blocking: `T` leapfrog steps per pass over HBM.
+//
+// A block owns an output tile of TX x TY sites in the x-y plane and a chunk of z-planes.  It
+// loads the tile plus a T-site halo on every side (the region, RX x RY columns) and streams
+// the region along z.  Stage s (s = 1..T) computes step s for plane i - s while plane i is
+// being loaded, so the T steps form a wavefront that lags one plane per stage:
+//
+//     iteration i:  load phi_0, pi, comp of plane i
+//                   stage 1 -> phi_1(i-1), stage 2 -> phi_2(i-2), ..., stage T -> phi_T(i-T)
+//
+// Each thread owns CX adjacent columns of one region row for every stage, so for its own
+// columns the centre and the z-neighbours of level s-1 (planes q-1, q, q+1) and the queues of
+// pi and comp (planes i .. i-T) stay in registers.  The x-y neighbours of level s-1 come from
+// shared memory, where every level keeps two plane buffers: stage s reads the plane that
+// stage s-1 wrote in the previous iteration and writes its own into the other buffer, so one
+// __syncthreads per iteration orders everything.  Level s is exact on the region shrunk by s
+// sites on each side (the periodic images of the halo were loaded, Sec. 3.3.1); the values
+// outside are never read by an exact site, and only the centre tile of level T is stored.
+//
+// The z-direction works the same way: to produce planes [z0, z1) at level T the chunk loads
+// planes [z0 - T, z1 + T) (wrapped) and each stage computes the planes it is exact on.
+//
+// pi and comp of halo columns are read by the neighbouring blocks too, so this kernel reads
+// phi, pi, comp from the front buffers and writes all three to the back buffers.
+#include "lf2_internal.cuh"
+
+namespace lf2 {
+namespace tb {
+
+constexpr int kTbMaxThreads = 512;
+
+template <int BYTES>
+struct VecOf;
+template <>
+struct VecOf<4> {
+    using T = float;
+};
+template <>
+struct VecOf<8> {
+    using T = float2;
+};
+template <>
+struct VecOf<16> {
+    using T = float4;
+};
+
+// N contiguous elements of R as one vector access (N * sizeof(R) in {4, 8, 16}).
+template <typename R, int N>
+__device__ __forceinline__ void vload_g(const R *__restrict__ p, R (&v)[N]) {
+    using V = typename VecOf<N * sizeof(R)>::T;
+    V t = __ldg(reinterpret_cast<const V *>(p));
+    memcpy(v, &t, sizeof(V));
+}
+template <typename R, int N>
+__device__ __forceinline__ void vload_cg(const R *__restrict__ p, R (&v)[N]) {
+    using V = typename VecOf<N * sizeof(R)>::T;
+    V t = __ldcg(reinterpret_cast<const V *>(p));
+    memcpy(v, &t, sizeof(V));
+}
+template <typename R, int N>
+__device__ __forceinline__ void vstore_g(R *__restrict__ p, const R (&v)[N]) {
+    using V = typename VecOf<N * sizeof(R)>::T;
+    V t;
+    memcpy(&t, v, sizeof(V));
+    *reinterpret_cast<V *>(p) = t;
+}
+template <typename R, int N>
+__device__ __forceinline__ void vload_s(const R *p, R (&v)[N]) {
+    using V = typename VecOf<N * sizeof(R)>::T;
+    V t = *reinterpret_cast<const V *>(p);
+    memcpy(v, &t, sizeof(V));
+}
+template <typename R, int N>
+__device__ __forceinline__ void vstore_s(R *p, const R (&v)[N]) {
+    using V = typename VecOf<N * sizeof(R)>::T;
+    V t;
+    memcpy(&t, v, sizeof(V));
+    *reinterpret_cast<V *>(p) = t;
+}
+
+__device__ __forceinline__ int wrap_any(int v, int n) {
+    int w = v % n;
+    return w < 0 ? w + n : w;
+}
+
+// Per-thread state of the wavefront, kept in registers across iterations.
+template <typename R, int T, int W>
+struct TbState {
+    R lv[T][3][W];  // level l (0..T-1) of own columns at planes q-1, q, q+1 of stage l+1
+    R pq[T + 1][W]; // pi of own columns at planes i, i-1, ..., i-T (updated stage by stage)
+    R cq[T + 1][W]; // Kahan compensation, same planes
+    R pf_phi[W], pf_pi[W], pf_c[W];  // plane i+1, loaded one iteration ahead
+};
+
+// One z-iteration of the wavefront.  Level l of the plane written in this iteration lives at
+// cur + l * ps2, the one written in the previous iteration at prev + l * ps2 (both already
+// offset to this thread's own columns).
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+__device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__restrict__ cur, const R *__restrict__ prev,
+                                             int ps2, int row_e, const CoefT &k, bool load_next,
+                                             const R *__restrict__ nphi, const R *__restrict__ npi,
+                                             const float *__restrict__ ncomp, bool store, R *__restrict__ ophi,
+                                             R *__restrict__ opi, float *__restrict__ ocomp, bool shfl_x) {
+    constexpr int W = CX * NC;
+    R in_phi[W], in_pi[W], in_c[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        in_phi[e] = st.pf_phi[e];
+        in_pi[e] = st.pf_pi[e];
+        in_c[e] = st.pf_c[e];
+    }
+    if (load_next) {
+        vload_g<R, W>(nphi, st.pf_phi);
+        vload_cg<R, W>(npi, st.pf_pi);
+        if (MODE == 1) vload_cg<R, W>(reinterpret_cast<const R *>(ncomp), st.pf_c);
+    }
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        st.lv[0][0][e] = st.lv[0][1][e];
+        st.lv[0][1][e] = st.lv[0][2][e];
+        st.lv[0][2][e] = in_phi[e];
+    }
+#pragma unroll
+    for (int l = T; l > 0; --l)
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            st.pq[l][e] = st.pq[l - 1][e];
+            if (MODE == 1) st.cq[l][e] = st.cq[l - 1][e];
+        }
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        st.pq[0][e] = in_pi[e];
+        if (MODE == 1) st.cq[0][e] = in_c[e];
+    }
+    vstore_s<R, W>(cur, in_phi);
+
+#pragma unroll
+    for (int s = 1; s <= T; ++s) {
+        const R *src = prev + (s - 1) * ps2;
+        R up[W], dn[W], left[NC], right[NC], out[W];
+        vload_s<R, W>(src + row_e, up);
+        vload_s<R, W>(src - row_e, dn);
+        if (shfl_x) {
+            // region rows are whole lane groups: the x-neighbours are the adjacent lanes' own
+            // columns (at a row's ends the values are from another row, but those columns are
+            // outside every stage's exact region and their results are never read)
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                left[a] = __shfl_up_sync(0xffffffffu, st.lv[s - 1][1][(CX - 1) * NC + a], 1);
+                right[a] = __shfl_down_sync(0xffffffffu, st.lv[s - 1][1][a], 1);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                left[a] = src[a - NC];
+                right[a] = src[W + a];
+            }
+        }
+        if constexpr (MODE != 3 && NC == 2) {
+            // FP32 complex: the two components of a site form one f32x2 pair
+            const Coef32x2 k2 = make_coef32x2(k, k.zero);
+            const R *L = st.lv[s - 1][1];
+#pragma unroll
+            for (int j = 0; j < CX; ++j) {
+                const int e = 2 * j;
+                f32x2 p = pk2(st.pq[s][e], st.pq[s][e + 1]);
+                f32x2 cm = (MODE == 1) ? pk2(st.cq[s][e], st.cq[s][e + 1]) : 0ull;
+                f32x2 o;
+                update_f32_site2<MODE == 1>(
+                    pk2(L[e], L[e + 1]), (j == 0) ? pk2(left[0], left[1]) : pk2(L[e - 2], L[e - 1]),
+                    (j == CX - 1) ? pk2(right[0], right[1]) : pk2(L[e + 2], L[e + 3]), pk2(dn[e], dn[e + 1]),
+                    pk2(up[e], up[e + 1]), pk2(st.lv[s - 1][0][e], st.lv[s - 1][0][e + 1]),
+                    pk2(st.lv[s - 1][2][e], st.lv[s - 1][2][e + 1]), p, cm, o, k2, k);
+                up2(o, out[e], out[e + 1]);
+                up2(p, st.pq[s][e], st.pq[s][e + 1]);
+                if (MODE == 1) up2(cm, st.cq[s][e], st.cq[s][e + 1]);
+            }
+        } else if constexpr (MODE != 3 && CX % 2 == 0) {
+            // FP32: two columns per packed f32x2 instruction stream
+            const Coef32x2 k2 = make_coef32x2(k, k.zero);
+#pragma unroll
+            for (int m = 0; m < CX / 2; ++m) {
+                const int j0 = 2 * m, j1 = 2 * m + 1;
+                f32x2 c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], o[NC];
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e0 = j0 * NC + a, e1 = j1 * NC + a;
+                    const R *L = st.lv[s - 1][1];
+                    c[a] = pk2(L[e0], L[e1]);
+                    xm[a] = pk2((j0 == 0) ? left[a] : L[e0 - NC], L[e0]);
+                    xp[a] = pk2(L[e1], (j1 == CX - 1) ? right[a] : L[e1 + NC]);
+                    ym[a] = pk2(dn[e0], dn[e1]);
+                    yp[a] = pk2(up[e0], up[e1]);
+                    zm[a] = pk2(st.lv[s - 1][0][e0], st.lv[s - 1][0][e1]);
+                    zp[a] = pk2(st.lv[s - 1][2][e0], st.lv[s - 1][2][e1]);
+                    p[a] = pk2(st.pq[s][e0], st.pq[s][e1]);
+                    cm[a] = (MODE == 1) ? pk2(st.cq[s][e0], st.cq[s][e1]) : 0ull;
+                }
+                update_f32x2<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, o, k2);
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e0 = j0 * NC + a, e1 = j1 * NC + a;
+                    up2(o[a], out[e0], out[e1]);
+                    up2(p[a], st.pq[s][e0], st.pq[s][e1]);
+                    if (MODE == 1) up2(cm[a], st.cq[s][e0], st.cq[s][e1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CX; ++j) {
+                R c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], o[NC];
+    #pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e = j * NC + a;
+                    c[a] = st.lv[s - 1][1][e];
+                    xm[a] = (j == 0) ? left[a] : st.lv[s - 1][1][e - NC];
+                    xp[a] = (j == CX - 1) ? right[a] : st.lv[s - 1][1][e + NC];
+                    ym[a] = dn[e];
+                    yp[a] = up[e];
+                    zm[a] = st.lv[s - 1][0][e];
+                    zp[a] = st.lv[s - 1][2][e];
+                    p[a] = st.pq[s][e];
+                    cm[a] = (MODE == 1) ? (float)st.cq[s][e] : 0.0f;
+                }
+                if constexpr (MODE == 3) {
+                    update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, o, k);
+                } else {
+                    update_f32<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, o, k);
+                }
+    #pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e = j * NC + a;
+                    out[e] = o[a];
+                    st.pq[s][e] = p[a];
+                    if (MODE == 1) st.cq[s][e] = cm[a];
+                }
+            }
+        }
+        if (s < T) {
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                st.lv[s][0][e] = st.lv[s][1][e];
+                st.lv[s][1][e] = st.lv[s][2][e];
+                st.lv[s][2][e] = out[e];
+            }
+            vstore_s<R, W>(cur + s * ps2, out);
+        } else if (store) {
+            vstore_g<R, W>(ophi, out);
+            vstore_g<R, W>(opi, st.pq[T]);
+            if (MODE == 1) vstore_g<R, W>(reinterpret_cast<R *>(ocomp), st.cq[T]);
+        }
+    }
+    __syncthreads();
+}
+
+// MODE: 0 = FP32 plain drift, 1 = FP32 Kahan drift, 3 = FP64.
+// Light configurations (shallow, narrow) are held to 64 registers so two blocks fit per SM.
+template <typename R, int NC, int T, int CX>
+constexpr int tb_min_blocks() {
+    return (T <= 4 && CX * NC * sizeof(R) <= 8) ? 2 : 1;
+}
+
+// One tile x z-chunk of a temporal-blocking pass: (bx, by) is the tile, bz the chunk.
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+__device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restrict__ phi_out, const R *__restrict__ pi,
+                                         R *__restrict__ pi_out, const float *__restrict__ comp,
+                                         float *__restrict__ comp_out, const Geom &g, const CoefT &k, int TX, int TY,
+                                         int zchunk, int bx, int by, int bz) {
+    constexpr int TP = ((T + CX - 1) / CX) * CX;  // x halo, rounded to whole thread groups
+    constexpr int W = CX * NC;                     // elements per thread per plane
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+
+    const int RX = TX + 2 * TP, RY = TY + 2 * T;
+    const int RXT = RX / CX;
+    const int ps = (RY + 2) * RX * NC;  // elements per shared plane (one padding row above and below)
+    const int t = threadIdx.x;
+    const int tx = t % RXT, ry = t / RXT;
+    const int rx0 = tx * CX;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int z0 = bz * zchunk;
+    const int z1 = min(z0 + zchunk, g.nz);
+
+    const int gx0 = wrap_any(x0 - TP + rx0, g.nx);
+    const int gy = wrap_any(y0 - T + ry, g.ny);
+    const long long planeE = (long long)g.nx * g.ny * NC;
+    const int colE = (gy * g.nx + gx0) * NC;  // offset within a plane (< 2^31 for every lattice run here)
+    const bool out_col =
+        rx0 >= TP && rx0 < TP + TX && x0 + rx0 - TP < g.nx && ry >= T && ry < T + TY && y0 + ry - T < g.ny;
+    const int s_own = ((ry + 1) * RX + rx0) * NC;
+    const int row_e = RX * NC;
+
+    TbState<R, T, W> st;
+#pragma unroll
+    for (int l = 0; l < T; ++l)
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int e = 0; e < W; ++e) st.lv[l][m][e] = R(0);
+#pragma unroll
+    for (int l = 0; l <= T; ++l)
+#pragma unroll
+        for (int e = 0; e < W; ++e) st.pq[l][e] = st.cq[l][e] = R(0);
+#pragma unroll
+    for (int e = 0; e < W; ++e) st.pf_c[e] = R(0);
+
+    // plane index of the next load, advanced with a compare instead of a modulo
+    int pl = wrap_any(z0 - T, g.nz);
+    {
+        const long long off = (long long)pl * planeE + colE;
+        vload_g<R, W>(phi + off, st.pf_phi);
+        vload_cg<R, W>(pi + off, st.pf_pi);
+        if (MODE == 1) vload_cg<R, W>(reinterpret_cast<const R *>(comp) + off, st.pf_c);
+    }
+    const int ibeg = z0 - T, iend = z1 + T;
+    // output plane of stage T in iteration i is i - T; stores start at i = z0 + T
+    long long out_off = (long long)(z0 - 2 * T - 1) * planeE + colE;  // advanced before each use
+    R *const base = sm + s_own;
+    // x-neighbours by warp shuffle when every region row is a whole group of lanes within one
+    // warp and the block is whole warps
+    const bool shfl_x = (32 % RXT == 0) && ((RXT * RY) % 32 == 0);
+    for (int i = ibeg; i < iend; ++i) {
+        pl = (pl + 1 == g.nz) ? 0 : pl + 1;
+        const long long noff = (long long)pl * planeE + colE;
+        out_off += planeE;
+        const int par = i & 1;
+        tb_iteration<R, NC, MODE, T, CX>(st, base + par * ps, base + (par ^ 1) * ps, 2 * ps, row_e, k, i + 1 < iend,
+                                         phi + noff, pi + noff, comp + noff, out_col && i - T >= z0,
+                                         phi_out + out_off, pi_out + out_off, comp_out + out_off, shfl_x);
+    }
+}
+
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+__global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>()))
+    k_tblock(const R *__restrict__ phi, R *__restrict__ phi_out, const R *__restrict__ pi, R *__restrict__ pi_out,
+             const float *__restrict__ comp, float *__restrict__ comp_out, Geom g, CoefT k, int TX, int TY,
+             int zchunk) {
+    tb_block<R, NC, MODE, T, CX, CoefT>(phi, phi_out, pi, pi_out, comp, comp_out, g, k, TX, TY, zchunk, blockIdx.x,
+                                        blockIdx.y, blockIdx.z);
+}
+
+// Ensemble pass: one launch covers the tiles of every member lattice.  The blocks walk a
+// shared work list (longest chunks first) with a fixed stride, so the assignment is
+// deterministic; members are independent, so no block waits on another.
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+__global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>()))
+    k_tblock_ensemble(const TbMember *__restrict__ members, const int4 *__restrict__ items, int nitems, int flip,
+                      int TX, int TY) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const TbMember &m = members[w.x];
+        const int f = m.front ^ flip;
+        CoefT k;
+        if constexpr (MODE == 3)
+            k = m.k64;
+        else
+            k = m.k32;
+        tb_block<R, NC, MODE, T, CX, CoefT>((const R *)m.phi[f], (R *)m.phi[f ^ 1], (const R *)m.pi[f],
+                                            (R *)m.pi[f ^ 1], m.comp[f], const_cast<float *>(m.comp[f ^ 1]), m.g, k, TX, TY, m.zchunk,
+                                            w.y, w.z, w.w);
+        __syncthreads();
+    }
+}
+
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+cudaError_t launch_t(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStream_t s) {
+    constexpr int TP = ((T + CX - 1) / CX) * CX;
+    const int RX = c.tile_x + 2 * TP, RY = c.tile_y + 2 * T;
+    const int threads = (RX / CX) * RY;
+    const size_t smem = (size_t)2 * T * (RY + 2) * RX * NC * sizeof(R);
+    auto kern = k_tblock<R, NC, MODE, T, CX, CoefT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.g.nx + c.tile_x - 1) / c.tile_x, (a.g.ny + c.tile_y - 1) / c.tile_y,
+              (a.g.nz + c.zchunk - 1) / c.zchunk);
+    kern<<<grid, threads, smem, s>>>((const R *)a.phi, (R *)a.phi_out, (const R *)a.pi, (R *)a.pi_out, a.comp,
+                                     a.comp_out, a.g, k, c.tile_x, c.tile_y, c.zchunk);
+    return cudaGetLastError();
+}
+
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+cudaError_t launch_ens_t(const TbEnsembleLaunch &e, cudaStream_t s) {
+    constexpr int TP = ((T + CX - 1) / CX) * CX;
+    const int RX = e.c.tile_x + 2 * TP, RY = e.c.tile_y + 2 * T;
+    const int threads = (RX / CX) * RY;
+    const size_t smem = (size_t)2 * T * (RY + 2) * RX * NC * sizeof(R);
+    auto kern = k_tblock_ensemble<R, NC, MODE, T, CX, CoefT>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (err != cudaSuccess) return err;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = (per_sm > 0 ? per_sm : 1) * sms;
+    if (grid > e.nitems) grid = e.nitems;
+    if (grid < 1) return cudaSuccess;
+    kern<<<grid, threads, smem, s>>>(e.members, e.items, e.nitems, e.flip, e.c.tile_x, e.c.tile_y);
+    return cudaGetLastError();
+}
+
+
+// Launches a depth-T pass (single lattice) or an ensemble pass for one storage type and mode;
+// each precision's instantiations live in their own translation unit.
+template <typename R, int NC, int MODE, typename CoefT>
+cudaError_t launch_prec(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStream_t s) {
+    switch (c.cx * 16 + c.depth) {
+#define LF2_TB_CASE(CXV, TV)                                                                      \
+    case CXV * 16 + TV:                                                                           \
+        if constexpr (CXV * NC * sizeof(R) <= 16) return launch_t<R, NC, MODE, TV, CXV, CoefT>(a, c, k, s); \
+        return cudaErrorNotSupported;
+        LF2_TB_CASE(1, 2) LF2_TB_CASE(1, 3) LF2_TB_CASE(1, 4) LF2_TB_CASE(1, 6) LF2_TB_CASE(1, 8)
+        LF2_TB_CASE(2, 2) LF2_TB_CASE(2, 3) LF2_TB_CASE(2, 4) LF2_TB_CASE(2, 6) LF2_TB_CASE(2, 8)
+        LF2_TB_CASE(4, 2) LF2_TB_CASE(4, 3) LF2_TB_CASE(4, 4) LF2_TB_CASE(4, 6) LF2_TB_CASE(4, 8)
+#undef LF2_TB_CASE
+        default: return cudaErrorNotSupported;
+    }
+}
+
+template <typename R, int NC, int MODE, typename CoefT>
+cudaError_t launch_ens_prec(const TbEnsembleLaunch &e, cudaStream_t s) {
+    switch (e.c.cx * 16 + e.c.depth) {
+#define LF2_TB_CASE(CXV, TV)                                                                      \
+    case CXV * 16 + TV:                                                                           \
+        if constexpr (CXV * NC * sizeof(R) <= 16) return launch_ens_t<R, NC, MODE, TV, CXV, CoefT>(e, s); \
+        return cudaErrorNotSupported;
+        LF2_TB_CASE(1, 2) LF2_TB_CASE(1, 3) LF2_TB_CASE(1, 4) LF2_TB_CASE(1, 6) LF2_TB_CASE(1, 8)
+        LF2_TB_CASE(2, 2) LF2_TB_CASE(2, 3) LF2_TB_CASE(2, 4) LF2_TB_CASE(2, 6) LF2_TB_CASE(2, 8)
+        LF2_TB_CASE(4, 2) LF2_TB_CASE(4, 3) LF2_TB_CASE(4, 4) LF2_TB_CASE(4, 6) LF2_TB_CASE(4, 8)
+#undef LF2_TB_CASE
+        default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace tb
+}  // namespace lf2

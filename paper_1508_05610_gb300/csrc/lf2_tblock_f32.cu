@@ -1,0 +1,17 @@
+// lf2_tblock_f32.cu -- temporal-blocking instantiations for plain FP32 (one translation unit per
+// precision so that the kernels compile in parallel).
+#include "lf2_tblock.cuh"
+
+namespace lf2 {
+
+cudaError_t launch_tblock_f32(const TbArgs &a, const TbConfig &c, cudaStream_t s) {
+    const Coef32 k = make_coef32(a.p, a.dt);
+    return a.ncomp == 1 ? tb::launch_prec<float, 1, 0>(a, c, k, s) : tb::launch_prec<float, 2, 0>(a, c, k, s);
+}
+
+cudaError_t launch_tblock_ensemble_f32(const TbEnsembleLaunch &e, cudaStream_t s) {
+    return e.ncomp == 1 ? tb::launch_ens_prec<float, 1, 0, Coef32>(e, s)
+                        : tb::launch_ens_prec<float, 2, 0, Coef32>(e, s);
+}
+
+}  // namespace lf2
