@@ -115,6 +115,106 @@ def test_256cube_complex_energy_of_inputs(env, ora):
             assert abs(e["sum_sq"][a] - oe["sum_sq"][a]) <= tol * oe["sum_sq"][a], prec
 
 
+def evolve_wrapped_tuned(torch, lf2, phi_t, prec, p, steps):
+    """Evolves a device tensor in place with every buffer borrowed and the tuner's plan (the
+    configuration the benchmark and the error study run); returns (phi, pi) tensors."""
+    nz, ny, nx, c = phi_t.shape
+    bufs = [phi_t, torch.empty_like(phi_t)]
+    if prec == lf2.LF2_F32_KAHAN:
+        bufs += [torch.zeros_like(phi_t), torch.zeros_like(phi_t)]
+    pis = [torch.zeros_like(phi_t), torch.empty_like(phi_t)]
+    lat = lf2.lf2_lattice_create((nx, ny, nz))
+    fphi = lf2.lf2_field_wrap(lat, c, prec, [t.data_ptr() for t in bufs])
+    fpi = lf2.lf2_field_wrap(lat, c, prec, [t.data_ptr() for t in pis])
+    try:
+        stream = torch.cuda.current_stream()
+        lf2.lf2_leapfrog_init(fphi, fpi, p, stream)
+        lf2.lf2_tune(fphi, fpi, p, stream=stream)
+        lf2.lf2_leapfrog(fphi, fpi, p, steps, stream)
+        torch.cuda.synchronize()
+        fp, fq = lf2.lf2_field_buffer(fphi, 0), lf2.lf2_field_buffer(fpi, 0)
+    finally:
+        lf2.lf2_field_free(fphi)
+        lf2.lf2_field_free(fpi)
+        lf2.lf2_lattice_destroy(lat)
+    phi = next(t for t in bufs if t.data_ptr() == fp)
+    pi = next(t for t in pis if t.data_ptr() == fq)
+    return phi, pi
+
+
+def test_1536cube_complex_fp32_kahan_tuned_sampled(env, ora):
+    """1536^3 complex phi^4, FP32 with the compensated drift and the tuned temporal-blocking plan
+    (the largest lattice of the workloads): sampled sites within 1e-5 of the FP64 oracle after 10
+    steps.  The oracle's boxes are cut from the initial field before it is evolved in place, so
+    the device holds one state (174 GB with temporal-blocking buffers)."""
+    torch, lf2 = env
+    torch.cuda.empty_cache()
+    n = 1536
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi = inputs.gaussian_field_device(n, n, n, 2, sigma=0.1, seed=inputs.BASE_SEED, dtype=torch.float32)
+    sites = sample_sites(n, 8, seed=3)
+    boxes = [box_of(torch, phi, c, HALF) for c in sites]
+    out_phi, out_pi = evolve_wrapped_tuned(torch, lf2, phi, lf2.LF2_F32_KAHAN, lf2.params(**kw), STEPS)
+    for center, box in zip(sites, boxes):
+        bphi, bpi = ora.evolve(box, np.zeros_like(box), STEPS, half_kick=True, **kw)
+        x, y, z = center
+        got_phi = out_phi[z, y, x].double().cpu().numpy()
+        got_pi = out_pi[z, y, x].double().cpu().numpy()
+        assert np.max(np.abs(got_phi - bphi[HALF, HALF, HALF])) <= 1e-5 * np.max(np.abs(bphi)), center
+        assert np.max(np.abs(got_pi - bpi[HALF, HALF, HALF])) <= 1e-5 * np.max(np.abs(bpi)), center
+    del phi, out_phi, out_pi
+    torch.cuda.empty_cache()
+
+
+def test_ensemble_of_64_lattices_members_match_standalone(env):
+    """The 64-lattice ensemble (sides from {64, 96, 128, 160, 192}, lambda ~ U[0.5, 2], FP32 with
+    the compensated drift, per-lattice seeds): after one tuned ensemble run, every member is
+    bitwise equal to the same lattice evolved alone with the one-thread-per-site kernel."""
+    torch, lf2 = env
+    torch.cuda.empty_cache()
+    members = inputs.ensemble_members()
+    steps = 13
+    stream = torch.cuda.current_stream()
+    keep, fields, plist = [], [], []
+    try:
+        for side, lam, seed in members:
+            phi = inputs.gaussian_field_device(side, side, side, 1, sigma=0.1, seed=seed, dtype=torch.float32)
+            lat = lf2.lf2_lattice_create((side, side, side))
+            fphi = lf2.lf2_field_alloc(lat, 1, lf2.LF2_F32_KAHAN)
+            fpi = lf2.lf2_field_alloc(lat, 1, lf2.LF2_F32_KAHAN)
+            torch.cuda.synchronize()
+            # copy the generated field into the library buffer through a borrowed view
+            tmp = lf2.lf2_field_wrap(lat, 1, lf2.LF2_F32_KAHAN, [phi.data_ptr()])
+            host = lf2.lf2_field_download(tmp, (side, side, side, 1))
+            lf2.lf2_field_free(tmp)
+            lf2.lf2_field_upload(fphi, host)
+            p = lf2.params(dx=1.0, dt=0.05, lam=lam, eta=1.0)
+            keep.append(host)
+            fields.append((lat, fphi, fpi))
+            plist.append(p)
+        e = lf2.lf2_ensemble_create([f[1] for f in fields], [f[2] for f in fields], plist)
+        try:
+            lf2.lf2_ensemble_tune(e, stream=stream)
+            lf2.lf2_ensemble_run(e, steps, stream)
+            torch.cuda.synchronize()
+            for i in (0, 1, 17, 40, 63):  # a spread of members and sizes
+                side = members[i][0]
+                got = (lf2.lf2_field_download(fields[i][1], (side, side, side, 1)),
+                       lf2.lf2_field_download(fields[i][2], (side, side, side, 1)))
+                with lf2.System((side, side, side), 1, "f32k") as s:
+                    s.upload(keep[i], np.zeros_like(keep[i]))
+                    lf2.lf2_leapfrog_ex(s.phi, s.pi, plist[i], steps, kernel=lf2.LF2_KERNEL_SITE)
+                    ref = s.download()
+                assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), i
+        finally:
+            lf2.lf2_ensemble_destroy(e)
+    finally:
+        for lat, fphi, fpi in fields:
+            lf2.lf2_field_free(fphi)
+            lf2.lf2_field_free(fpi)
+            lf2.lf2_lattice_destroy(lat)
+
+
 def test_1024cube_real_grf_fp32_kahan_sampled(env, ora):
     """1024^3 real phi^4 from a Gaussian random field with P(k) ~ k^-2 cut at pi/4, FP32 with
     the compensated drift, dt=0.05: sampled sites within 1e-5 of the FP64 oracle after 10 steps,
