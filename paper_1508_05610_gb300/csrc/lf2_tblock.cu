@@ -34,11 +34,22 @@ bool tblock_supported(const TbArgs &a, TbConfig &c) {
     const size_t smem = (size_t)2 * c.depth * (RY + 2) * RX * a.ncomp * esz;
     if (smem > 227 * 1024) return false;
     if (c.zchunk == 0) {
-        // enough blocks for about two waves at one block per SM
+        // Split z into m chunks, m minimising (waves of blocks) x (iterations per block): a
+        // chunk of zc planes costs zc + 2 depth iterations, and with one block per SM a launch
+        // takes ceil(blocks / 152) waves.  More chunks shrink the last, partly filled wave
+        // but add the 2 depth halo planes per chunk.
         const long long tiles = (long long)((a.g.nx + c.tile_x - 1) / c.tile_x) * ((a.g.ny + c.tile_y - 1) / c.tile_y);
-        int zc = a.g.nz;
-        while (zc > 4 * c.depth && tiles * ((a.g.nz + zc - 1) / zc) < 152 * 2) zc = (zc + 1) / 2;
-        c.zchunk = zc;
+        long long best = -1;
+        for (int m = 1; m <= 64; ++m) {
+            const int zc = (a.g.nz + m - 1) / m;
+            if (m > 1 && zc < 2 * c.depth) break;
+            const long long blocks = tiles * ((a.g.nz + zc - 1) / zc);
+            const long long cost = ((blocks + 151) / 152) * (zc + 2 * c.depth);
+            if (best < 0 || cost < best) {
+                best = cost;
+                c.zchunk = zc;
+            }
+        }
     }
     if (c.zchunk < 1) return false;
     const uintptr_t align = (uintptr_t)c.cx * a.ncomp * esz;

@@ -67,7 +67,8 @@ void append_file(const Key &k, const lf2_step_config &c) {
 
 std::vector<lf2_step_config> candidates(lf2_precision prec, int flags) {
     std::vector<lf2_step_config> out;
-    for (int ty : {4, 8}) out.push_back(lf2_step_config{LF2_KERNEL_STREAM, 0, ty, 0, 0, 0});
+    for (int ty : {4, 8})
+        for (int zc : {4, 8, 16}) out.push_back(lf2_step_config{LF2_KERNEL_STREAM, 0, ty, zc, 0, 0});
     if (flags & LF2_TUNE_ONE_STEP) return out;
     const int depths64[] = {2, 4};
     const int depths32[] = {2, 3, 4, 6, 8};
