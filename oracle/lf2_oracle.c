@@ -337,6 +337,34 @@ int ora_evolve(int nx, int ny, int nz, int ncomp, const double *params, double *
     return ORA_OK;
 }
 
+/* First-order symmetric difference along dimension i, the paper's example of Site use
+ * (Sec. 3.4): d_a(x) = (phi_a(x+i) - phi_a(x-i)) / (2 dx), for every component, into a second
+ * field -- the "field operation" the paper benchmarks (Sec. 4.2). */
+int ora_derivative(int nx, int ny, int nz, int ncomp, int dim, double dx, const double *phi_host,
+                   double *out_host) {
+    const int sizes[3] = {nx, ny, nz};
+    ora_lattice lat;
+    if (check_shape(nx, ny, nz, ncomp) || lattice_init(&lat, sizes, 1) || dim < 0 || dim > 2 || !(dx > 0.0))
+        return ORA_EINVAL;
+    ora_field phi, out;
+    if (field_alloc(&phi, &lat, ncomp)) return ORA_ENOMEM;
+    if (field_alloc(&out, &lat, ncomp)) {
+        field_free(&phi);
+        return ORA_ENOMEM;
+    }
+    field_load(&phi, phi_host);
+    update_halo(&phi);
+    ora_site x;
+    for (site_first(&x, &lat); site_test(&x); site_next(&x))
+        for (int a = 0; a < ncomp; ++a)
+            out.data[x.index * ncomp + a] =
+                (phi.data[site_up(&x, dim) * ncomp + a] - phi.data[site_dn(&x, dim) * ncomp + a]) / (2.0 * dx);
+    field_store(&out, out_host);
+    field_free(&phi);
+    field_free(&out);
+    return ORA_OK;
+}
+
 /* Energy and checksums at integer step n from phi_n and pi_{n-1/2}.
  * out[0..3] = kinetic, gradient, potential, total (each with the dx^3 volume element);
  * out[4..4+ncomp) = sum_x phi_a;  out[4+ncomp..4+2 ncomp) = sum_x phi_a^2.              */

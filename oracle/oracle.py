@@ -50,7 +50,8 @@ def _load():
             lib.ora_force.argtypes = [i, i, i, i, dp, dp, dp]
             lib.ora_evolve.argtypes = [i, i, i, i, dp, dp, dp, i, i, i]
             lib.ora_energy.argtypes = [i, i, i, i, dp, dp, dp, dp]
-            for f in (lib.ora_update_halo, lib.ora_force, lib.ora_evolve, lib.ora_energy):
+            lib.ora_derivative.argtypes = [i, i, i, i, i, ctypes.c_double, dp, dp]
+            for f in (lib.ora_update_halo, lib.ora_force, lib.ora_evolve, lib.ora_energy, lib.ora_derivative):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -120,6 +121,15 @@ def energy(phi, pi, dx=1.0, dt=0.1, lam=1.0, eta=1.0, m2=0.0) -> dict:
                               _ptr(out)), "energy")
     return {"kinetic": out[0], "gradient": out[1], "potential": out[2], "total": out[3],
             "sum": out[4:4 + c].copy(), "sum_sq": out[4 + c:4 + 2 * c].copy()}
+
+
+def derivative(phi, dim, dx=1.0) -> np.ndarray:
+    """(phi_a(x + i) - phi_a(x - i)) / (2 dx) along dimension dim (0 = x) for every component."""
+    a = _field(phi)
+    nz, ny, nx, c = a.shape
+    out = np.empty_like(a)
+    _check(_load().ora_derivative(nx, ny, nz, c, int(dim), float(dx), _ptr(a), _ptr(out)), "derivative")
+    return out
 
 
 def light_cone_box(field: np.ndarray, center, half: int) -> np.ndarray:

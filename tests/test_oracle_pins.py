@@ -353,3 +353,42 @@ def test_threads_bitwise_and_light_cone_box(ora):
         cx, cy, cz = center
         assert np.array_equal(bphi[half, half, half], full[cz, cy, cx])
         assert np.array_equal(bpi[half, half, half], fpi[cz, cy, cx])
+
+
+# ------------------------------------------------- O(N) fields and the derivative operation
+@pytest.mark.parametrize("ncomp", [3, 6])
+def test_on_components_dispersion_and_coupling(ora, ncomp):
+    """N-component fields: with lambda = 0 each component follows its own plane-wave dispersion;
+    with lambda != 0 a homogeneous field's force couples all components through |phi|^2."""
+    shape, dt, m2 = (8, 12, 16), 0.1, 0.2
+    waves = [plane_wave(shape, (a % 3 + 1, (a + 1) % 3, a % 2), 0.3 + 0.1 * a, 0.2 * a) for a in range(ncomp)]
+    phi0 = np.stack(waves, axis=-1)
+    phi, _ = ora.evolve(phi0, np.zeros_like(phi0), 200, dt=dt, lam=0.0, m2=m2, half_kick=True)
+    for a in range(ncomp):
+        modes = (a % 3 + 1, (a + 1) % 3, a % 2)
+        w = 2.0 / dt * math.asin(lattice_omega(shape, modes, 1.0, m2) * dt / 2.0)
+        assert np.max(np.abs(phi[..., a] - waves[a] * math.cos(200 * w * dt))) <= 1e-12
+    vals = np.arange(1, ncomp + 1, dtype=np.float64) * 0.5
+    hom = np.broadcast_to(vals, (3, 3, 3, ncomp)).copy()
+    F = ora.force(hom, lam=0.5, eta=1.0, m2=0.0)
+    s2 = float(np.sum(vals * vals))
+    assert np.allclose(F, -0.5 * vals * (s2 - 1.0), rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("dim", [0, 1, 2])
+def test_derivative_bruteforce_and_plane_wave(ora, dim):
+    nz, ny, nx = 5, 6, 7
+    phi = inputs.integer_field(nx, ny, nz, 3, seed=81)
+    d = ora.derivative(phi, dim, dx=0.5)
+    axis = 2 - dim  # arrays are (z, y, x, c)
+    want = (np.roll(phi, -1, axis=axis) - np.roll(phi, 1, axis=axis)) / (2 * 0.5)
+    assert np.array_equal(d, want)
+    # plane wave: (cos(u + k) - cos(u - k)) / 2 = -sin(k) sin(u), with k along dim
+    shape, modes = (16, 12, 8), [0, 0, 0]
+    modes[dim] = 1
+    w = plane_wave(shape, tuple(modes), 1.0, 0.3)[..., None]
+    n_dim = (shape[2], shape[1], shape[0])[dim]
+    k = 2 * np.pi / n_dim
+    z, y, x = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), np.arange(shape[2]), indexing="ij")
+    u = 2 * np.pi * (modes[0] * x / shape[2] + modes[1] * y / shape[1] + modes[2] * z / shape[0]) + 0.3
+    assert np.max(np.abs(ora.derivative(w, dim)[..., 0] + math.sin(k) * np.sin(u))) <= 1e-14
