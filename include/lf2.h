@@ -6,7 +6,8 @@
  * The method (the paper describes the data model; the equation of motion is the standard one
  * for the classical field simulations the library was written for, Sec. 1 and Sec. 5):
  *
- *   field      phi_a(x), a = 0 .. ncomp-1 (ncomp = 1: real, 2: complex as two reals)
+ *   field      phi_a(x), a = 0 .. ncomp-1 (ncomp = 1: real, 2: complex as two reals,
+ *              up to LF2_MAX_COMP: an O(N)-symmetric N-component field)
  *   potential  V = lambda/4 (sum_b phi_b^2 - eta^2)^2 + m2/2 sum_a phi_a^2
  *   force      F_a(x) = (1/dx^2) sum_{i=0..2} [phi_a(x+i) + phi_a(x-i) - 2 phi_a(x)]
  *                       - lambda phi_a (sum_b phi_b^2 - eta^2) - m2 phi_a
@@ -61,6 +62,10 @@ typedef enum {
 
 typedef enum { LF2_F64 = 0, LF2_F32_KAHAN = 1, LF2_F32 = 2 } lf2_precision;
 
+/* Most components a field may have.  1 and 2 run on every kernel; 3 to 6 on the
+ * one-thread-per-site kernel. */
+#define LF2_MAX_COMP 6
+
 typedef struct lf2_lattice_s *lf2_lattice;
 typedef struct lf2_field_s *lf2_field;
 typedef struct lf2_ensemble_s *lf2_ensemble;
@@ -80,8 +85,8 @@ typedef struct {
     double gradient;  /* dx^3 sum_x sum_a sum_i (phi_a(x+i) - phi_a(x))^2 / (2 dx^2) */
     double potential; /* dx^3 sum_x V(phi(x)) */
     double total;     /* kinetic + gradient + potential */
-    double sum[2];    /* sum_x phi_a(x) per component (unused entries 0) */
-    double sum_sq[2]; /* sum_x phi_a(x)^2 per component (unused entries 0) */
+    double sum[LF2_MAX_COMP];    /* sum_x phi_a(x) per component (unused entries 0) */
+    double sum_sq[LF2_MAX_COMP]; /* sum_x phi_a(x)^2 per component (unused entries 0) */
 } lf2_energy_t;
 
 /* Kernel selection for lf2_leapfrog_ex.  Every variant computes bitwise the same result. */
@@ -119,8 +124,8 @@ lf2_status lf2_lattice_sites(lf2_lattice lat, long long *out);
 /* ------------------------------------------------------------------------ field */
 
 /* Field<T>(lat, comp) of Sec. 3.3: allocates one device buffer of sites*ncomp elements of
- * the precision's storage type, zero-filled.  ncomp must be 1 or 2 (LF2_ERR_UNSUPPORTED
- * otherwise).  A field used as phi by lf2_leapfrog also gets a back buffer and, for
+ * the precision's storage type, zero-filled.  1 <= ncomp <= LF2_MAX_COMP
+ * (LF2_ERR_UNSUPPORTED above).  A field used as phi by lf2_leapfrog also gets a back buffer and, for
  * LF2_F32_KAHAN, a zeroed float compensation buffer; they are allocated by
  * lf2_leapfrog_init or, failing that, by the first lf2_leapfrog on the field -- before any
  * stream capture.  The library owns these buffers. */
@@ -153,6 +158,26 @@ lf2_status lf2_field_upload(lf2_field f, const double *host, void *stream);
 
 /* Copies the field's current values to sites*ncomp host doubles; synchronises `stream`. */
 lf2_status lf2_field_download(lf2_field f, double *host, void *stream);
+
+/* Binary snapshot in LATfield2's write/read format (Sec. 3.5): one file, no header, sites in
+ * row-major order with each site's components together.  Elements are written in the field's
+ * storage type (double for LF2_F64, float otherwise), so a snapshot is exact.  which = 0
+ * writes the current values, which = 2 the Kahan compensation of an LF2_F32_KAHAN phi field.
+ * Synchronises `stream`; LF2_ERR_INVALID on I/O errors (message in lf2_last_error). */
+lf2_status lf2_field_write(lf2_field f, int which, const char *path, void *stream);
+
+/* Reads a snapshot written by lf2_field_write (or any file of that layout and element type)
+ * into the current values (which = 0) or the compensation (which = 2).  The file size must
+ * match the field exactly.  Reading values resets the compensation to zero; read the
+ * compensation afterwards for an exact restart.  Synchronises `stream`. */
+lf2_status lf2_field_read(lf2_field f, int which, const char *path, void *stream);
+
+/* The first-order symmetric difference along dimension dim (0 = x, 1 = y, 2 = z), the
+ * paper's example of Site neighbours (Sec. 3.4) and the field operation of its benchmarks
+ * (Sec. 4.2): dst_a(x) = (src_a(x + dim) - src_a(x - dim)) / (2 dx) for every component, with
+ * periodic wrap.  src and dst: same lattice, components and precision, different fields.
+ * Computed in the storage precision. */
+lf2_status lf2_field_derivative(lf2_field src, lf2_field dst, int dim, double dx, void *stream);
 
 /* updateHalo() of Sec. 3.3.1.  The GPU kernels read periodic images by wrapped indexing,
  * so there is no stored halo to refresh: this validates the handle and returns LF2_OK. */
@@ -187,8 +212,8 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
  * pool or host framework that forbids cudaMalloc while it runs) or that must make no
  * allocation call at all.  lf2_energy allocates scratch and a pinned result buffer on its
  * first call for a field; this variant allocates nothing: no cudaMalloc, cudaFree, pinned-host
- * or library allocation.  Its scratch is one fixed array inside the library (608 x 8 + 8
- * doubles, 39 KB) that every GPU which loads the library holds until the process exits.  The
+ * or library allocation.  Its scratch is one fixed array inside the library (608 x 16 + 16
+ * doubles, 78 KB) that every GPU which loads the library holds until the process exits.  The
  * reduction's grid is fixed, so every lattice fits; if the scratch needed ever exceeded the
  * array, the call would return LF2_ERR_UNSUPPORTED with a message.  The first call on a device
  * looks up the array's device address (make it before any stream capture).  All calls share

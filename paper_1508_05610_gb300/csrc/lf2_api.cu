@@ -73,7 +73,7 @@ lf2_status new_field(lf2_lattice lat, int ncomp, int prec, lf2_field *out) {
     if (!lat || !out) return fail(LF2_ERR_INVALID, "lattice or output pointer is NULL");
     if (!valid_prec(prec)) return fail(LF2_ERR_INVALID, "unknown precision %d", prec);
     if (ncomp < 1) return fail(LF2_ERR_INVALID, "ncomp must be >= 1");
-    if (ncomp > kMaxComp) return fail(LF2_ERR_UNSUPPORTED, "ncomp %d not built (1 or 2)", ncomp);
+    if (ncomp > kMaxComp) return fail(LF2_ERR_UNSUPPORTED, "ncomp %d not built (1 to %d)", ncomp, kMaxComp);
     return LF2_OK;
 }
 
@@ -137,12 +137,13 @@ lf2_status ensure_tblock(lf2_field phi, lf2_field pi, cudaStream_t s) {
 lf2_status ensure_energy_scratch(lf2_field f) {
     if (!f->energy_scratch) {
         void *d = nullptr;
-        LF2_CUDA(cudaMalloc(&d, sizeof(double) * (kEnergyBlocks * 8 + 8)), "cudaMalloc(energy scratch)");
+        LF2_CUDA(cudaMalloc(&d, sizeof(double) * (kEnergyBlocks * kEnergySlots + kEnergySlots)),
+                 "cudaMalloc(energy scratch)");
         f->energy_scratch = (double *)d;
     }
     if (!f->energy_host) {
         void *h = nullptr;
-        LF2_CUDA(cudaMallocHost(&h, sizeof(double) * 8), "cudaMallocHost(energy result)");
+        LF2_CUDA(cudaMallocHost(&h, sizeof(double) * kEnergySlots), "cudaMallocHost(energy result)");
         f->energy_host = (double *)h;
     }
     return LF2_OK;
@@ -380,6 +381,19 @@ lf2_status lf2_field_download(lf2_field f, double *host, void *stream) {
     return LF2_OK;
 }
 
+lf2_status lf2_field_derivative(lf2_field src, lf2_field dst, int dim, double dx, void *stream) {
+    if (!src || !dst) return fail(LF2_ERR_INVALID, "field handle is NULL");
+    if (src == dst) return fail(LF2_ERR_INVALID, "src and dst must be different fields");
+    if (src->lat != dst->lat || src->ncomp != dst->ncomp || src->prec != dst->prec)
+        return fail(LF2_ERR_INVALID, "src and dst differ in lattice, components or precision");
+    if (dim < 0 || dim > 2) return fail(LF2_ERR_INVALID, "dim must be 0, 1 or 2");
+    if (!(dx > 0.0) || !std::isfinite(dx)) return fail(LF2_ERR_INVALID, "dx must be finite and > 0");
+    LF2_CUDA(launch_derivative(src->val[src->front], dst->val[dst->front], geom_of(src->lat), src->ncomp, src->prec,
+                               dim, dx, (cudaStream_t)stream),
+             "derivative launch");
+    return LF2_OK;
+}
+
 lf2_status lf2_field_update_halo(lf2_field f, void *stream) {
     (void)stream;
     if (!f) return fail(LF2_ERR_INVALID, "field is NULL");
@@ -473,11 +487,12 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
     if (st != LF2_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     double *partials = phi->energy_scratch;
-    double *result = phi->energy_scratch + kEnergyBlocks * 8;
+    double *result = phi->energy_scratch + kEnergyBlocks * kEnergySlots;
     LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
                            result, s),
              "energy launch");
-    LF2_CUDA(cudaMemcpyAsync(phi->energy_host, result, 8 * sizeof(double), cudaMemcpyDeviceToHost, s), "energy copy");
+    LF2_CUDA(cudaMemcpyAsync(phi->energy_host, result, kEnergySlots * sizeof(double), cudaMemcpyDeviceToHost, s),
+             "energy copy");
     LF2_CUDA(cudaStreamSynchronize(s), "energy sync");
     const double *r = phi->energy_host;
     const double vol = p->dx * p->dx * p->dx;
@@ -489,7 +504,7 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
     e.total = e.kinetic + e.gradient + e.potential;
     for (int a = 0; a < phi->ncomp; ++a) {
         e.sum[a] = r[3 + a];
-        e.sum_sq[a] = r[5 + a];
+        e.sum_sq[a] = r[3 + kMaxComp + a];
     }
     *out = e;
     return LF2_OK;
@@ -500,8 +515,8 @@ lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, 
     if (st == LF2_OK) st = check_params(p);
     if (st != LF2_OK) return st;
     if (!out) return fail(LF2_ERR_INVALID, "output pointer is NULL");
-    // The reduction writes one partial per block of its fixed grid, then 8 results.
-    const long long needed = (long long)kEnergyBlocks * 8 + 8;
+    // The reduction writes one partial row per block of its fixed grid, then one result row.
+    const long long needed = (long long)kEnergyBlocks * kEnergySlots + kEnergySlots;
     if (needed > kEnergyNoallocDoubles)
         return fail(LF2_ERR_UNSUPPORTED, "energy reduction needs %lld scratch doubles, the fixed array holds %d",
                     needed, kEnergyNoallocDoubles);
@@ -509,13 +524,13 @@ lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, 
     LF2_CUDA(energy_noalloc_scratch(&scratch), "cudaGetSymbolAddress(energy scratch)");
     cudaStream_t s = (cudaStream_t)stream;
     double *partials = scratch;
-    double *result = scratch + kEnergyBlocks * 8;
+    double *result = scratch + kEnergyBlocks * kEnergySlots;
     // Every slot read below is written earlier in the same call, so nothing left over from a
     // previous call is used and nothing needs clearing.
     LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
                            result, s),
              "energy launch");
-    double r[8];
+    double r[kEnergySlots];
     LF2_CUDA(cudaMemcpyAsync(r, result, sizeof r, cudaMemcpyDeviceToHost, s), "energy copy");
     LF2_CUDA(cudaStreamSynchronize(s), "energy sync");
     const double vol = p->dx * p->dx * p->dx;
@@ -527,7 +542,7 @@ lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, 
     e.total = e.kinetic + e.gradient + e.potential;
     for (int a = 0; a < phi->ncomp; ++a) {
         e.sum[a] = r[3 + a];
-        e.sum_sq[a] = r[5 + a];
+        e.sum_sq[a] = r[3 + kMaxComp + a];
     }
     *out = e;
     return LF2_OK;

@@ -20,7 +20,7 @@
 namespace lf2 {
 namespace {
 
-constexpr int kSlots = 8;
+constexpr int kSlots = kEnergySlots;
 
 template <typename R, int NC>
 __device__ __forceinline__ void load_d(const R *__restrict__ f, long long s, double (&v)[NC]) {
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(const R *__restrict__
             const double ex = xp[a] - c[a], ey = yp[a] - c[a], ez = zp[a] - c[a];
             acc[1] += 0.5 * k.inv_dx2 * ((ex * ex + ey * ey) + ez * ez);
             acc[3 + a] += c[a];
-            acc[5 + a] += c[a] * c[a];
+            acc[3 + kMaxComp + a] += c[a] * c[a];
         }
         acc[2] += 0.25 * k.lam * w * w + 0.5 * k.m2 * s2;
     }
@@ -102,10 +102,13 @@ template <typename R>
 cudaError_t launch_typed(const void *phi, const void *pi, const Geom &g, int ncomp, const CoefE &k, double *partials,
                          double *result, cudaStream_t s) {
     const int nb = kEnergyBlocks;
-    if (ncomp == 1)
-        k_energy<R, 1><<<nb, kEnergyThreads, 0, s>>>((const R *)phi, (const R *)pi, g, k, partials);
-    else
-        k_energy<R, 2><<<nb, kEnergyThreads, 0, s>>>((const R *)phi, (const R *)pi, g, k, partials);
+    switch (ncomp) {
+#define LF2_E(NC) \
+    case NC: k_energy<R, NC><<<nb, kEnergyThreads, 0, s>>>((const R *)phi, (const R *)pi, g, k, partials); break;
+        LF2_E(1) LF2_E(2) LF2_E(3) LF2_E(4) LF2_E(5) LF2_E(6)
+#undef LF2_E
+        default: return cudaErrorInvalidValue;
+    }
     k_energy_final<<<1, kEnergyThreads, 0, s>>>(partials, nb, result);
     return cudaGetLastError();
 }
@@ -124,7 +127,7 @@ cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int nc
 // framework owns the device allocator, or that must not make allocation calls at all.
 // lf2_energy allocates its partial-sum scratch on first use; lf2_energy_noalloc uses this
 // file-scope array instead.  Every GPU that loads the library holds it until process exit.
-// It holds the per-block partials of the reduction's fixed grid plus the 8 results; the grid
+// It holds the per-block partials of the reduction's fixed grid plus one result row; the grid
 // does not depend on the lattice, so the capacity is a constant.
 static __device__ __align__(256) double g_energy_noalloc[kEnergyNoallocDoubles];
 

@@ -14,7 +14,7 @@
 
 namespace lf2 {
 
-constexpr int kMaxComp = 2;
+constexpr int kMaxComp = LF2_MAX_COMP;
 
 // ---------------------------------------------------------------- coefficient packs
 // FP64: the force enters only through dt*F, folded as
@@ -274,10 +274,13 @@ cudaError_t launch_site_step(const StepArgs &a, cudaStream_t s);
 bool stream_supported(const StepArgs &a, int tile_y, int zchunk);
 cudaError_t launch_stream_step(const StepArgs &a, int tile_y, int zchunk, int nsteps_hint, cudaStream_t s);
 
-// Energy: writes 8 doubles to `result` (device): kin, grad, pot (without dx^3),
-// sum[0], sum[1], sumsq[0], sumsq[1], unused.  `partials` holds kEnergyBlocks*8 doubles.
+// Energy: writes kEnergySlots doubles to `result` (device): kin, grad, pot (without dx^3),
+// sum[a] at 3 + a, sum_sq[a] at 3 + kMaxComp + a.  `partials` holds kEnergyBlocks x
+// kEnergySlots doubles.
 constexpr int kEnergyBlocks = 152 * 4;
 constexpr int kEnergyThreads = 256;
+constexpr int kEnergySlots = 16;
+static_assert(3 + 2 * kMaxComp <= kEnergySlots, "energy slots");
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
                           const lf2_params &p, double *partials, double *result, cudaStream_t s);
 
@@ -328,12 +331,16 @@ cudaError_t launch_tblock_ensemble(const TbEnsembleLaunch &e, cudaStream_t s);
 bool tblock_supported(const TbArgs &a, TbConfig &c);
 cudaError_t launch_tblock(const TbArgs &a, const TbConfig &c, cudaStream_t s);
 
-// Fixed-size scratch of lf2_energy_noalloc: kEnergyBlocks*8 partials + 8 results (39 KB).
-constexpr int kEnergyNoallocDoubles = kEnergyBlocks * 8 + 8;
+// Fixed-size scratch of lf2_energy_noalloc: the partials plus one result row (78 KB).
+constexpr int kEnergyNoallocDoubles = kEnergyBlocks * kEnergySlots + kEnergySlots;
 cudaError_t energy_noalloc_scratch(double **out);
 
 // Conversions between host-side doubles and storage precision.
 cudaError_t launch_convert_from_f64(const double *src, void *dst, long long n, lf2_precision prec, cudaStream_t s);
 cudaError_t launch_convert_to_f64(const void *src, double *dst, long long n, lf2_precision prec, cudaStream_t s);
+
+// First-order symmetric difference along `dim` into dst (same layout), in storage precision.
+cudaError_t launch_derivative(const void *src, void *dst, const Geom &g, int ncomp, lf2_precision prec, int dim,
+                              double dx, cudaStream_t s);
 
 }  // namespace lf2

@@ -226,6 +226,7 @@ int default_zchunk(const StepArgs &a, int by) {
 bool stream_supported(const StepArgs &a, int tile_y, int zchunk) {
     const int by = tile_y ? tile_y : kDefaultBY;
     if (by != 2 && by != 4 && by != 8 && by != 16) return false;
+    if (a.ncomp > 2) return false;
     const int esz = a.prec == LF2_F64 ? 8 : 4;
     if (((long long)a.g.nx * a.ncomp * esz) % 16) return false;
     if (a.g.ny % by) return false;

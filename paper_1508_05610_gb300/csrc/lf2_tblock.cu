@@ -16,6 +16,7 @@ constexpr int kTbMaxThreads = 512;  // the kernels' launch bound
 }  // namespace
 
 bool tblock_supported(const TbArgs &a, TbConfig &c) {
+    if (a.ncomp > 2) return false;
     if (c.depth == 0) c.depth = 4;
     if (c.depth != 2 && c.depth != 3 && c.depth != 4 && c.depth != 6 && c.depth != 8) return false;
     const int esz = a.prec == LF2_F64 ? 8 : 4;

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "liblf2.so")
 
 LF2_OK, LF2_ERR_INVALID, LF2_ERR_UNSUPPORTED, LF2_ERR_NOMEM, LF2_ERR_CUDA, LF2_ERR_TIMEOUT, LF2_ERR_STATE = range(7)
 LF2_F64, LF2_F32_KAHAN, LF2_F32 = 0, 1, 2
+LF2_MAX_COMP = 6
 LF2_KERNEL_AUTO, LF2_KERNEL_SITE, LF2_KERNEL_STREAM, LF2_KERNEL_TBLOCK = 0, 1, 2, 3
 
 PRECISIONS = {"f64": LF2_F64, "f32k": LF2_F32_KAHAN, "f32": LF2_F32}
@@ -30,7 +31,7 @@ class lf2_params(ctypes.Structure):
 
 class lf2_energy_t(ctypes.Structure):
     _fields_ = [("kinetic", ctypes.c_double), ("gradient", ctypes.c_double), ("potential", ctypes.c_double),
-                ("total", ctypes.c_double), ("sum", ctypes.c_double * 2), ("sum_sq", ctypes.c_double * 2)]
+                ("total", ctypes.c_double), ("sum", ctypes.c_double * 6), ("sum_sq", ctypes.c_double * 6)]
 
     def as_dict(self, ncomp=2):
         return {"kinetic": self.kinetic, "gradient": self.gradient, "potential": self.potential,
@@ -67,6 +68,9 @@ SIGNATURES = {
     "lf2_field_upload": [_vp, ctypes.POINTER(ctypes.c_double), _vp],
     "lf2_field_download": [_vp, ctypes.POINTER(ctypes.c_double), _vp],
     "lf2_field_update_halo": [_vp, _vp],
+    "lf2_field_derivative": [_vp, _vp, ctypes.c_int, ctypes.c_double, _vp],
+    "lf2_field_write": [_vp, ctypes.c_int, ctypes.c_char_p, _vp],
+    "lf2_field_read": [_vp, ctypes.c_int, ctypes.c_char_p, _vp],
     "lf2_leapfrog_init": [_vp, _vp, ctypes.POINTER(lf2_params), _vp],
     "lf2_leapfrog": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, _vp],
     "lf2_leapfrog_ex": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, ctypes.POINTER(lf2_step_config), _vp],
@@ -173,6 +177,18 @@ def lf2_field_download(f, shape, stream=None, out=None) -> np.ndarray:
     a = np.empty(shape, dtype=np.float64) if out is None else out
     _call("lf2_field_download", f, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_ptr(stream))
     return a
+
+
+def lf2_field_write(f, path, which=0, stream=None):
+    _call("lf2_field_write", f, int(which), os.fsencode(path), _stream_ptr(stream))
+
+
+def lf2_field_read(f, path, which=0, stream=None):
+    _call("lf2_field_read", f, int(which), os.fsencode(path), _stream_ptr(stream))
+
+
+def lf2_field_derivative(src, dst, dim, dx=1.0, stream=None):
+    _call("lf2_field_derivative", src, dst, int(dim), float(dx), _stream_ptr(stream))
 
 
 def lf2_field_update_halo(f, stream=None):

@@ -27,6 +27,9 @@ def main(argv=None):
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--op", default="leapfrog", choices=["leapfrog", "derivative"],
+                    help="derivative: time lf2_field_derivative along --dim instead of leapfrog steps")
+    ap.add_argument("--dim", type=int, default=0)
     args = ap.parse_args(argv)
 
     import torch
@@ -49,6 +52,28 @@ def main(argv=None):
     lat = lf2.lf2_lattice_create((nx, ny, nz))
     fphi = lf2.lf2_field_wrap(lat, args.ncomp, prec, [t.data_ptr() for t in bufs])
     fpi = lf2.lf2_field_wrap(lat, args.ncomp, prec, [t.data_ptr() for t in pis])
+    if args.op == "derivative":
+        out = torch.empty_like(phi)
+        fout = lf2.lf2_field_wrap(lat, args.ncomp, prec, [out.data_ptr()])
+        try:
+            for _ in range(args.warmup):
+                lf2.lf2_field_derivative(fphi, fout, args.dim, 1.0, stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.steps):
+                lf2.lf2_field_derivative(fphi, fout, args.dim, 1.0, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3 / args.steps
+        finally:
+            for f in (fout, fphi, fpi):
+                lf2.lf2_field_free(f)
+            lf2.lf2_lattice_destroy(lat)
+        nbytes = 2 * phi.numel() * phi.element_size()  # read src once, write dst once
+        print(json.dumps({"op": "derivative", "lattice": [nx, ny, nz], "ncomp": args.ncomp, "prec": args.prec,
+                          "dim": args.dim, "seconds_per_call": t, "algorithmic_GBps": nbytes / t / 1e9}))
+        return
     try:
         lf2.lf2_leapfrog_init(fphi, fpi, p, stream)
         if args.kernel == "tune":

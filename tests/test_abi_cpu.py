@@ -75,7 +75,7 @@ def test_field_argument_checks_before_any_device_call(lib):
     lat = lib.lf2_lattice_create([4, 4, 4])
     try:
         with pytest.raises(lib.LF2Error) as e:
-            lib.lf2_field_alloc(lat, 3, lib.LF2_F64)
+            lib.lf2_field_alloc(lat, 7, lib.LF2_F64)
         assert e.value.status == lib.LF2_ERR_UNSUPPORTED
         with pytest.raises(lib.LF2Error) as e:
             lib.lf2_field_alloc(lat, 0, lib.LF2_F64)

@@ -218,3 +218,62 @@ def test_tblock_fp64_parity_with_oracle(lf2, ora):
     phi, pi, _ = run_gpu(lf2, phi0, pi0, 10, "f64", kw, kernel=lf2.LF2_KERNEL_TBLOCK, depth=4, cx=1, tile_x=16,
                          tile_y=8)
     assert relmax(phi, ophi) <= F64_TOL and relmax(pi, opi) <= F64_TOL
+
+
+# ------------------------------------------------ O(N) fields with 3 to 6 components
+@pytest.mark.parametrize("ncomp", [3, 4, 6])
+def test_n_component_fields_fp64_parity(lf2, ora, ncomp):
+    nx, ny, nz = 12, 10, 8
+    kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.3, seed=111)
+    pi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=112)
+    ophi, opi = ora.evolve(phi0, pi0, 10, half_kick=True, **kw)
+    oe = ora.energy(ophi, opi, **kw)
+    phi, pi, e = run_gpu(lf2, phi0, pi0, 10, "f64", kw)
+    assert relmax(phi, ophi) <= F64_TOL and relmax(pi, opi) <= F64_TOL
+    assert abs(e["total"] - oe["total"]) <= F64_TOL * abs(oe["total"])
+    assert np.allclose(e["sum_sq"], oe["sum_sq"], rtol=F64_TOL, atol=0)
+    scale = float(np.sum(np.abs(ophi)))
+    assert np.all(np.abs(e["sum"] - oe["sum"]) <= F64_TOL * scale)
+
+
+@pytest.mark.parametrize("prec", ["f32k", "f32"])
+def test_n_component_fields_fp32_and_integer_bitwise(lf2, ora, prec):
+    nx, ny, nz, ncomp = 12, 10, 8, 3
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.2, seed=113)
+    ophi, opi = ora.evolve(phi0, np.zeros_like(phi0), 10, half_kick=True, **kw)
+    phi, pi, _ = run_gpu(lf2, phi0, np.zeros_like(phi0), 10, prec, kw)
+    assert relmax(phi, ophi) <= 1e-5 and relmax(pi, opi) <= 1e-5
+    ikw = dict(dx=1.0, dt=1.0, lam=0.0, eta=0.0, m2=0.0)
+    i0 = inputs.integer_field(nx, ny, nz, 6, lo=-4, hi=4, seed=114)
+    j0 = inputs.integer_field(nx, ny, nz, 6, lo=-4, hi=4, seed=115)
+    ophi, opi = ora.evolve(i0, j0, 4, **ikw)
+    phi, pi, _ = run_gpu(lf2, i0, j0, 4, prec, ikw, half_kick=False)
+    assert np.array_equal(phi, ophi) and np.array_equal(pi, opi)
+
+
+# ------------------------------------------------ the paper's field operation: derivative
+@pytest.mark.parametrize("prec,ncomp", [("f64", 1), ("f64", 3), ("f32", 2), ("f32k", 6)])
+@pytest.mark.parametrize("dim", [0, 1, 2])
+def test_derivative_matches_oracle(lf2, ora, prec, ncomp, dim):
+    nx, ny, nz = 20, 12, 9
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=1.0, seed=120 + dim)
+    # integer data with dx = 0.5 (1/(2 dx) = 1): exact in every precision
+    i0 = inputs.integer_field(nx, ny, nz, ncomp, seed=130 + dim)
+    for data, dx, exact in ((i0, 0.5, True), (phi0, 0.7, False)):
+        with lf2.System((nx, ny, nz), ncomp, prec) as src:
+            dst = lf2.lf2_field_alloc(src.lat, ncomp, src.prec)  # a second field on the same Lattice
+            try:
+                lf2.lf2_field_upload(src.phi, data)
+                stored = lf2.lf2_field_download(src.phi, src.host_shape)  # the values the GPU holds
+                lf2.lf2_field_derivative(src.phi, dst, dim, dx)
+                got = lf2.lf2_field_download(dst, src.host_shape)
+            finally:
+                lf2.lf2_field_free(dst)
+        want = ora.derivative(stored, dim, dx=dx)
+        if exact:
+            assert np.array_equal(got, want)
+        else:
+            tol = 1e-15 if prec == "f64" else 2e-7
+            assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))

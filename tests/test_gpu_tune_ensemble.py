@@ -138,3 +138,41 @@ def test_ensemble_tune_and_configs_bitwise(lf2):
     finally:
         for s in systems:
             s.close()
+
+
+@pytest.mark.parametrize("prec,ncomp", [("f64", 2), ("f32k", 1), ("f32", 2)])
+def test_snapshot_format_and_exact_restart(lf2, tmp_path, prec, ncomp):
+    """Snapshots are the paper's header-less row-major per-site component lists in the storage
+    type; writing phi, pi (and the compensation) and reading them into fresh fields continues
+    the run bit for bit."""
+    shape = (24, 20, 16)
+    nx, ny, nz = shape
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.4, seed=71)
+    p = lf2.params(**kw)
+    dtype = np.float64 if prec == "f64" else np.float32
+    straight = run_site(lf2, shape, ncomp, prec, phi0, np.zeros_like(phi0), kw, 20)
+    with lf2.System(shape, ncomp, prec) as s:
+        s.upload(phi0, np.zeros_like(phi0))
+        lf2.lf2_leapfrog_ex(s.phi, s.pi, p, 10, kernel=lf2.LF2_KERNEL_SITE)
+        lf2.lf2_field_write(s.phi, tmp_path / "phi.bin")
+        lf2.lf2_field_write(s.pi, tmp_path / "pi.bin")
+        if prec == "f32k":
+            lf2.lf2_field_write(s.phi, tmp_path / "comp.bin", which=2)
+        # the file is the row-major per-site component list in the storage type
+        raw = np.fromfile(tmp_path / "phi.bin", dtype=dtype).reshape(nz, ny, nx, ncomp)
+        assert np.array_equal(raw.astype(np.float64), s.download()[0])
+    with lf2.System(shape, ncomp, prec) as s:
+        lf2.lf2_field_read(s.phi, tmp_path / "phi.bin")
+        lf2.lf2_field_read(s.pi, tmp_path / "pi.bin")
+        if prec == "f32k":
+            lf2.lf2_field_read(s.phi, tmp_path / "comp.bin", which=2)
+        lf2.lf2_leapfrog_ex(s.phi, s.pi, p, 10, kernel=lf2.LF2_KERNEL_SITE)
+        got = s.download()
+    assert np.array_equal(got[0], straight[0]) and np.array_equal(got[1], straight[1])
+    # a file of the wrong size is rejected
+    (tmp_path / "short.bin").write_bytes(b"\0" * 8)
+    with lf2.System(shape, ncomp, prec) as s:
+        with pytest.raises(lf2.LF2Error) as e:
+            lf2.lf2_field_read(s.phi, tmp_path / "short.bin")
+        assert e.value.status == lf2.LF2_ERR_INVALID
