@@ -392,3 +392,23 @@ def test_derivative_bruteforce_and_plane_wave(ora, dim):
     z, y, x = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), np.arange(shape[2]), indexing="ij")
     u = 2 * np.pi * (modes[0] * x / shape[2] + modes[1] * y / shape[1] + modes[2] * z / shape[0]) + 0.3
     assert np.max(np.abs(ora.derivative(w, dim)[..., 0] + math.sin(k) * np.sin(u))) <= 1e-14
+
+
+# ------------------------------------------------------------- power spectrum (diagnostic)
+def test_power_spectrum_parseval_and_plane_wave(ora):
+    """Parseval: sum over modes of |phi~|^2 / V = sum_x phi^2, so sum_b P_b n_b equals the field's
+    sum of squares when every mode falls in a bin; a plane wave A cos(k.x) puts V A^2 / 2 of
+    power into the two modes +-k, i.e. the bin of |k| holds P = V A^2 / 4 per mode."""
+    N = 8
+    phi = inputs.gaussian_field(N, N, N, 2, sigma=1.0, seed=91)
+    P, K, n = ora.power_spectrum(phi, comp=1, nbins=64)
+    assert n.sum() == N ** 3
+    assert np.sum(P * n) == pytest.approx(np.sum(phi[..., 1] ** 2), rel=1e-12)
+    A, modes = 0.7, (2, 1, 3)
+    w = plane_wave((N, N, N), modes, A, 0.0)
+    P, K, n = ora.power_spectrum(w[..., None], nbins=64)
+    b = math.isqrt(sum(m * m for m in modes))
+    assert P[b] * n[b] == pytest.approx(N ** 3 * A * A / 2, rel=1e-12)
+    assert np.sum(P * n) == pytest.approx(N ** 3 * A * A / 2, rel=1e-12)
+    # mode counts of the first shells of an 8^3 lattice: |m|^2 = 0 | 1,2,3 | 4..8 ...
+    assert n[0] == 1 and n[1] == 6 + 12 + 8
