@@ -179,6 +179,16 @@ lf2_status lf2_field_read(lf2_field f, int which, const char *path, void *stream
  * Computed in the storage precision. */
 lf2_status lf2_field_derivative(lf2_field src, lf2_field dst, int dim, double dx, void *stream);
 
+/* Binned power spectrum of component `comp` of a field on a cubic N^3 lattice (the paper's
+ * FFT is for cubic lattices, Sec. 3.6): P(k) = |phi~(k)|^2 / N^3 with phi~(k) = sum_x phi(x)
+ * exp(-i k.x), k_i = 2 pi m_i / (N dx).  Mode (m_x, m_y, m_z) (signed integer frequencies)
+ * belongs to shell b = floor(sqrt(m_x^2 + m_y^2 + m_z^2)); shells b < nbins (<= 1024) are
+ * returned as host arrays of nbins doubles: mean power, mean |k|, mode count.  The transform is
+ * cuFFT (single or double precision after the storage type); buffers and the plan are
+ * allocated per call.  LF2_ERR_UNSUPPORTED for non-cubic lattices.  Synchronises `stream`. */
+lf2_status lf2_power_spectrum(lf2_field f, int comp, int nbins, double dx, double *power, double *kmean,
+                              double *count, void *stream);
+
 /* updateHalo() of Sec. 3.3.1.  The GPU kernels read periodic images by wrapped indexing,
  * so there is no stored halo to refresh: this validates the handle and returns LF2_OK. */
 lf2_status lf2_field_update_halo(lf2_field f, void *stream);

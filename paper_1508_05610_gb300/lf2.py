@@ -68,6 +68,8 @@ SIGNATURES = {
     "lf2_field_upload": [_vp, ctypes.POINTER(ctypes.c_double), _vp],
     "lf2_field_download": [_vp, ctypes.POINTER(ctypes.c_double), _vp],
     "lf2_field_update_halo": [_vp, _vp],
+    "lf2_power_spectrum": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp],
     "lf2_field_derivative": [_vp, _vp, ctypes.c_int, ctypes.c_double, _vp],
     "lf2_field_write": [_vp, ctypes.c_int, ctypes.c_char_p, _vp],
     "lf2_field_read": [_vp, ctypes.c_int, ctypes.c_char_p, _vp],
@@ -185,6 +187,15 @@ def lf2_field_write(f, path, which=0, stream=None):
 
 def lf2_field_read(f, path, which=0, stream=None):
     _call("lf2_field_read", f, int(which), os.fsencode(path), _stream_ptr(stream))
+
+
+def lf2_power_spectrum(f, comp=0, nbins=32, dx=1.0, stream=None):
+    """(mean power, mean |k|, mode count) per shell b = floor(|m|), as numpy arrays."""
+    power, kmean, count = np.zeros(nbins), np.zeros(nbins), np.zeros(nbins)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _call("lf2_power_spectrum", f, int(comp), int(nbins), float(dx), power.ctypes.data_as(dp),
+          kmean.ctypes.data_as(dp), count.ctypes.data_as(dp), _stream_ptr(stream))
+    return power, kmean, count
 
 
 def lf2_field_derivative(src, dst, dim, dx=1.0, stream=None):
