@@ -217,6 +217,14 @@ lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int
  * synchronises `stream`. */
 lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream);
 
+/* lf2_energy without synchronising: enqueues the reduction on `stream` and writes one
+ * lf2_energy_t record (16 doubles, same layout) to the device memory at dev_out.  Allocates
+ * nothing and never waits, so step and energy calls can be captured together into a CUDA
+ * graph (for example a run with energies every step).  Uses the scratch that
+ * lf2_leapfrog_init or a first lf2_energy allocated on phi (LF2_ERR_STATE before that).
+ * Calls on one phi field share that scratch: order them on one stream. */
+lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, double *dev_out, void *stream);
+
 /* lf2_energy for callers that cannot allocate device memory.  The paper has no counterpart;
  * this entry point exists for callers whose device allocator belongs to someone else (a memory
  * pool or host framework that forbids cudaMalloc while it runs) or that must make no

@@ -510,6 +510,23 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
     return LF2_OK;
 }
 
+lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, double *dev_out, void *stream) {
+    lf2_status st = check_pair(phi, pi);
+    if (st == LF2_OK) st = check_params(p);
+    if (st != LF2_OK) return st;
+    if (!dev_out) return fail(LF2_ERR_INVALID, "output pointer is NULL");
+    if (!phi->energy_scratch)
+        return fail(LF2_ERR_STATE, "no energy scratch yet: call lf2_leapfrog_init or lf2_energy on phi first");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *partials = phi->energy_scratch;
+    double *result = phi->energy_scratch + kEnergyBlocks * kEnergySlots;
+    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p,
+                           partials, result, s),
+             "energy launch");
+    LF2_CUDA(launch_energy_record(result, p->dx * p->dx * p->dx, dev_out, s), "energy record");
+    return LF2_OK;
+}
+
 lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream) {
     lf2_status st = check_pair(phi, pi);
     if (st == LF2_OK) st = check_params(p);

@@ -122,6 +122,26 @@ cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int nc
     return launch_typed<float>(phi, pi, g, ncomp, k, partials, result, s);
 }
 
+// ------------------------------------------------------ device-side energy record
+// Turns the raw result row into an lf2_energy_t-shaped record in device memory: kinetic,
+// gradient, potential (times dx^3), total, sum[kMaxComp], sum_sq[kMaxComp].
+__global__ void k_energy_record(const double *__restrict__ r, double vol, double *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    out[0] = vol * r[0];
+    out[1] = vol * r[1];
+    out[2] = vol * r[2];
+    out[3] = out[0] + out[1] + out[2];
+    for (int a = 0; a < kMaxComp; ++a) {
+        out[4 + a] = r[3 + a];
+        out[4 + kMaxComp + a] = r[3 + kMaxComp + a];
+    }
+}
+
+cudaError_t launch_energy_record(const double *result, double vol, double *out, cudaStream_t s) {
+    k_energy_record<<<1, 32, 0, s>>>(result, vol, out);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------- fixed scratch for lf2_energy_noalloc
 // Some callers cannot allocate device memory: code that runs while a memory pool or another
 // framework owns the device allocator, or that must not make allocation calls at all.

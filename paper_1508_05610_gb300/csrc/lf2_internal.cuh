@@ -331,6 +331,10 @@ cudaError_t launch_tblock_ensemble(const TbEnsembleLaunch &e, cudaStream_t s);
 bool tblock_supported(const TbArgs &a, TbConfig &c);
 cudaError_t launch_tblock(const TbArgs &a, const TbConfig &c, cudaStream_t s);
 
+// Writes an lf2_energy_t-shaped record (16 doubles) from a result row to device memory.
+cudaError_t launch_energy_record(const double *result, double vol, double *out, cudaStream_t s);
+static_assert(sizeof(lf2_energy_t) == (4 + 2 * kMaxComp) * sizeof(double), "energy record layout");
+
 // Fixed-size scratch of lf2_energy_noalloc: the partials plus one result row (78 KB).
 constexpr int kEnergyNoallocDoubles = kEnergyBlocks * kEnergySlots + kEnergySlots;
 cudaError_t energy_noalloc_scratch(double **out);

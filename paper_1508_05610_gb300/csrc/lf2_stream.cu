@@ -29,23 +29,36 @@ struct Vec16<double> {
     static constexpr int E = 2;
 };
 
-template <typename R>
-__device__ __forceinline__ void ld16(const R *__restrict__ p, R (&v)[16 / sizeof(R)]) {
-    typename Vec16<R>::T t = __ldg(reinterpret_cast<const typename Vec16<R>::T *>(p));
-    memcpy(v, &t, 16);
+// NV consecutive 16-byte vectors (E = NV * 16 / sizeof(R) elements).
+template <typename R, int E>
+__device__ __forceinline__ void ld16(const R *__restrict__ p, R (&v)[E]) {
+    using VT = typename Vec16<R>::T;
+#pragma unroll
+    for (int q = 0; q < (int)(E * sizeof(R) / 16); ++q) {
+        VT t = __ldg(reinterpret_cast<const VT *>(p) + q);
+        memcpy(&v[q * (16 / sizeof(R))], &t, 16);
+    }
 }
 
-template <typename R>
-__device__ __forceinline__ void ldcg16(const R *__restrict__ p, R (&v)[16 / sizeof(R)]) {
-    typename Vec16<R>::T t = __ldcg(reinterpret_cast<const typename Vec16<R>::T *>(p));
-    memcpy(v, &t, 16);
+template <typename R, int E>
+__device__ __forceinline__ void ldcg16(const R *__restrict__ p, R (&v)[E]) {
+    using VT = typename Vec16<R>::T;
+#pragma unroll
+    for (int q = 0; q < (int)(E * sizeof(R) / 16); ++q) {
+        VT t = __ldcg(reinterpret_cast<const VT *>(p) + q);
+        memcpy(&v[q * (16 / sizeof(R))], &t, 16);
+    }
 }
 
-template <typename R>
-__device__ __forceinline__ void st16(R *__restrict__ p, const R (&v)[16 / sizeof(R)]) {
-    typename Vec16<R>::T t;
-    memcpy(&t, v, 16);
-    *reinterpret_cast<typename Vec16<R>::T *>(p) = t;
+template <typename R, int E>
+__device__ __forceinline__ void st16(R *__restrict__ p, const R (&v)[E]) {
+    using VT = typename Vec16<R>::T;
+#pragma unroll
+    for (int q = 0; q < (int)(E * sizeof(R) / 16); ++q) {
+        VT t;
+        memcpy(&t, &v[q * (16 / sizeof(R))], 16);
+        reinterpret_cast<VT *>(p)[q] = t;
+    }
 }
 
 template <typename R>
@@ -57,15 +70,24 @@ __device__ __forceinline__ R shfl_dn1(R v) {
     return __shfl_down_sync(0xffffffffu, v, 1);
 }
 
+// NV 16-byte vectors per thread and plane: 1 for one or two components; 3 for 3 or 6
+// components (and 2 for 4 FP64 components), so each thread holds whole sites.
+template <typename R, int NC>
+__host__ __device__ constexpr int stream_nv() {
+    return (16 / (int)sizeof(R)) % NC == 0 ? 1 : ((32 / (int)sizeof(R)) % NC == 0 ? 2 : 3);
+}
+
 // MODE: 0 = FP32 plain drift, 1 = FP32 Kahan drift, 3 = FP64.
 template <typename R, int NC, int MODE, int BY, typename CoefT>
 __global__ void __launch_bounds__(32 * BY) k_stream(const R *__restrict__ phi, R *__restrict__ phi_out,
                                                     R *__restrict__ pi, float *__restrict__ comp, Geom g, CoefT k,
                                                     int zchunk) {
-    constexpr int E = 16 / sizeof(R);  // elements per thread
-    constexpr int S = E / NC;          // sites per thread
+    constexpr int NV = stream_nv<R, NC>();
+    constexpr int E = NV * 16 / sizeof(R);  // elements per thread
+    constexpr int S = E / NC;               // sites per thread
+    static_assert(E % NC == 0, "whole sites per thread");
     using VT = typename Vec16<R>::T;
-    __shared__ VT sm[2][BY + 2][32];
+    __shared__ VT sm[2][BY + 2][32 * NV];
 
     const int lane = threadIdx.x, ty = threadIdx.y;
     const int xs = (blockIdx.x * 32 + lane) * S;  // first site of this thread
@@ -98,18 +120,18 @@ __global__ void __launch_bounds__(32 * BY) k_stream(const R *__restrict__ phi, R
 #pragma unroll
     for (int e = 0; e < E; ++e) below[e] = cur[e] = above[e] = R(0);
     if (active) {
-        ld16(phi + (long long)wrap_dn(z0, g.nz) * planeE + off_y, below);
-        ld16(phi + (long long)z0 * planeE + off_y, cur);
+        ld16<R, E>(phi + (long long)wrap_dn(z0, g.nz) * planeE + off_y, below);
+        ld16<R, E>(phi + (long long)z0 * planeE + off_y, cur);
     }
 
     for (int z = z0; z < z1; ++z) {
         const long long pz = (long long)z * planeE;
         R halo[E], pv[E], cv[E], lft[NC], rgt[NC];
         if (active) {
-            ld16(phi + (long long)wrap_up(z, g.nz) * planeE + off_y, above);
-            if (yh >= 0) ld16(phi + pz + off_h, halo);
-            ldcg16(pi + pz + off_y, pv);
-            if (MODE == 1) ldcg16(reinterpret_cast<const R *>(comp) + pz + off_y, cv);
+            ld16<R, E>(phi + (long long)wrap_up(z, g.nz) * planeE + off_y, above);
+            if (yh >= 0) ld16<R, E>(phi + pz + off_h, halo);
+            ldcg16<R, E>(pi + pz + off_y, pv);
+            if (MODE == 1) ldcg16<R, E>(reinterpret_cast<const R *>(comp) + pz + off_y, cv);
             if (lane == 0) {
 #pragma unroll
                 for (int a = 0; a < NC; ++a) lft[a] = __ldg(phi + pz + off_l + a);
@@ -120,13 +142,14 @@ __global__ void __launch_bounds__(32 * BY) k_stream(const R *__restrict__ phi, R
             }
         }
         const int buf = (z - z0) & 1;
-        {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
             VT t;
-            memcpy(&t, cur, 16);
-            sm[buf][ty + 1][lane] = t;
+            memcpy(&t, &cur[q * (16 / sizeof(R))], 16);
+            sm[buf][ty + 1][lane * NV + q] = t;
             if (yh >= 0) {
-                memcpy(&t, halo, 16);
-                sm[buf][hslot][lane] = t;
+                memcpy(&t, &halo[q * (16 / sizeof(R))], 16);
+                sm[buf][hslot][lane * NV + q] = t;
             }
         }
         // x-neighbours across lanes
@@ -139,11 +162,12 @@ __global__ void __launch_bounds__(32 * BY) k_stream(const R *__restrict__ phi, R
         }
         __syncthreads();
         R ymv[E], ypv[E];
-        {
-            VT t = sm[buf][ty][lane];
-            memcpy(ymv, &t, 16);
-            t = sm[buf][ty + 2][lane];
-            memcpy(ypv, &t, 16);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            VT t = sm[buf][ty][lane * NV + q];
+            memcpy(&ymv[q * (16 / sizeof(R))], &t, 16);
+            t = sm[buf][ty + 2][lane * NV + q];
+            memcpy(&ypv[q * (16 / sizeof(R))], &t, 16);
         }
         if (active) {
             R outv[E];
@@ -176,9 +200,9 @@ __global__ void __launch_bounds__(32 * BY) k_stream(const R *__restrict__ phi, R
                     if (MODE == 1) cv[e] = cm[a];
                 }
             }
-            st16(phi_out + pz + off_y, outv);
-            st16(pi + pz + off_y, pv);
-            if (MODE == 1) st16(reinterpret_cast<R *>(comp) + pz + off_y, cv);
+            st16<R, E>(phi_out + pz + off_y, outv);
+            st16<R, E>(pi + pz + off_y, pv);
+            if (MODE == 1) st16<R, E>(reinterpret_cast<R *>(comp) + pz + off_y, cv);
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -192,7 +216,7 @@ constexpr int kDefaultBY = 4;
 
 template <typename R, int NC, int MODE, int BY, typename CoefT>
 cudaError_t launch_t(const StepArgs &a, int zchunk, const CoefT &k, cudaStream_t s) {
-    constexpr int S = 16 / (int)sizeof(R) / NC;
+    constexpr int S = stream_nv<R, NC>() * 16 / (int)sizeof(R) / NC;
     dim3 block(32, BY);
     dim3 grid((a.g.nx + 32 * S - 1) / (32 * S), a.g.ny / BY, (a.g.nz + zchunk - 1) / zchunk);
     k_stream<R, NC, MODE, BY, CoefT><<<grid, block, 0, s>>>((const R *)a.phi, (R *)a.phi_out, (R *)a.pi, a.comp, a.g,
@@ -200,16 +224,31 @@ cudaError_t launch_t(const StepArgs &a, int zchunk, const CoefT &k, cudaStream_t
     return cudaGetLastError();
 }
 
+template <typename R, int MODE, int BY, typename CoefT>
+cudaError_t launch_nc(const StepArgs &a, int zchunk, const CoefT &k, cudaStream_t s) {
+    switch (a.ncomp) {
+        case 1: return launch_t<R, 1, MODE, BY>(a, zchunk, k, s);
+        case 2: return launch_t<R, 2, MODE, BY>(a, zchunk, k, s);
+        case 3: return launch_t<R, 3, MODE, BY>(a, zchunk, k, s);
+        case 4: return launch_t<R, 4, MODE, BY>(a, zchunk, k, s);
+        case 6: return launch_t<R, 6, MODE, BY>(a, zchunk, k, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
 template <int BY>
 cudaError_t launch_by(const StepArgs &a, int zchunk, cudaStream_t s) {
-    if (a.prec == LF2_F64) {
-        const Coef64 k = make_coef64(a.p, a.dt);
-        return a.ncomp == 1 ? launch_t<double, 1, 3, BY>(a, zchunk, k, s) : launch_t<double, 2, 3, BY>(a, zchunk, k, s);
-    }
+    if (a.prec == LF2_F64) return launch_nc<double, 3, BY>(a, zchunk, make_coef64(a.p, a.dt), s);
     const Coef32 k = make_coef32(a.p, a.dt);
-    if (a.prec == LF2_F32_KAHAN)
-        return a.ncomp == 1 ? launch_t<float, 1, 1, BY>(a, zchunk, k, s) : launch_t<float, 2, 1, BY>(a, zchunk, k, s);
-    return a.ncomp == 1 ? launch_t<float, 1, 0, BY>(a, zchunk, k, s) : launch_t<float, 2, 0, BY>(a, zchunk, k, s);
+    if (a.prec == LF2_F32_KAHAN) return launch_nc<float, 1, BY>(a, zchunk, k, s);
+    return launch_nc<float, 0, BY>(a, zchunk, k, s);
+}
+
+// sites per thread of the streaming kernel for this precision and component count
+int sites_per_thread(int esz, int ncomp) {
+    const int e1 = 16 / esz;
+    const int nv = e1 % ncomp == 0 ? 1 : ((2 * e1) % ncomp == 0 ? 2 : 3);
+    return nv * e1 / ncomp;
 }
 
 int default_zchunk(const StepArgs &a, int by) {
@@ -226,9 +265,10 @@ int default_zchunk(const StepArgs &a, int by) {
 bool stream_supported(const StepArgs &a, int tile_y, int zchunk) {
     const int by = tile_y ? tile_y : kDefaultBY;
     if (by != 2 && by != 4 && by != 8 && by != 16) return false;
-    if (a.ncomp > 2) return false;
+    if (a.ncomp == 5 || a.ncomp > 6) return false;
     const int esz = a.prec == LF2_F64 ? 8 : 4;
     if (((long long)a.g.nx * a.ncomp * esz) % 16) return false;
+    if (a.g.nx % sites_per_thread(esz, a.ncomp)) return false;  // whole thread chunks per row
     if (a.g.ny % by) return false;
     if (zchunk < 0) return false;
     if (!a.drift) return false;

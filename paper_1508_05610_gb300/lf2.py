@@ -77,6 +77,7 @@ SIGNATURES = {
     "lf2_leapfrog": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, _vp],
     "lf2_leapfrog_ex": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, ctypes.POINTER(lf2_step_config), _vp],
     "lf2_energy": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
+    "lf2_energy_device": [_vp, _vp, ctypes.POINTER(lf2_params), _vp, _vp],
     "lf2_energy_noalloc": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
     "lf2_ensemble_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(lf2_params),
                             ctypes.POINTER(_vp)],
@@ -224,6 +225,15 @@ def lf2_energy(phi, pi, p: lf2_params, stream=None, ncomp=2) -> dict:
     e = lf2_energy_t()
     _call("lf2_energy", phi, pi, ctypes.byref(p), ctypes.byref(e), _stream_ptr(stream))
     return e.as_dict(ncomp)
+
+
+def lf2_energy_device(phi, pi, p: lf2_params, dev_out_ptr, stream=None):
+    """Enqueues the energy reduction; writes an lf2_energy_t record to device memory."""
+    _call("lf2_energy_device", phi, pi, ctypes.byref(p), dev_out_ptr, _stream_ptr(stream))
+
+
+ENERGY_RECORD_FIELDS = ["kinetic", "gradient", "potential", "total"] + [f"sum{a}" for a in range(6)] + \
+    [f"sum_sq{a}" for a in range(6)]
 
 
 def lf2_energy_noalloc(phi, pi, p: lf2_params, stream=None, ncomp=2) -> dict:

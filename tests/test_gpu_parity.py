@@ -124,7 +124,8 @@ def test_integer_fields_bitwise_all_precisions(lf2, ora, prec, shape, ncomp):
 
 # ------------------------------------------- every kernel variant gives the same bits
 @pytest.mark.parametrize("prec", ["f64", "f32k", "f32"])
-@pytest.mark.parametrize("shape,ncomp", [((64, 16, 12), 1), ((32, 16, 10), 2), ((96, 8, 9), 1)])
+@pytest.mark.parametrize("shape,ncomp", [((64, 16, 12), 1), ((32, 16, 10), 2), ((96, 8, 9), 1), ((24, 16, 10), 3),
+                                         ((16, 8, 6), 6), ((12, 8, 5), 4), ((136, 8, 5), 3)])
 def test_kernel_variants_bitwise_identical(lf2, prec, shape, ncomp):
     nx, ny, nz = shape
     kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)

@@ -176,3 +176,47 @@ def test_snapshot_format_and_exact_restart(lf2, tmp_path, prec, ncomp):
         with pytest.raises(lf2.LF2Error) as e:
             lf2.lf2_field_read(s.phi, tmp_path / "short.bin")
         assert e.value.status == lf2.LF2_ERR_INVALID
+
+
+def test_32cube_run_with_energy_every_step_in_one_cuda_graph(lf2, ora):
+    """The 32^3 real FP64 workload (dt = 0.1, lambda = eta = 1, sigma = 0.1) with energy and
+    checksum after every one of 100 steps, captured into one CUDA graph (lf2_leapfrog +
+    lf2_energy_device per step) and replayed: every record within 1e-12 of the oracle."""
+    import torch
+    kw = dict(dx=1.0, dt=0.1, lam=1.0, eta=1.0, m2=0.0)
+    p = lf2.params(**kw)
+    phi0 = inputs.gaussian_field(32, 32, 32, 1, sigma=0.1, seed=inputs.BASE_SEED)
+    steps = 100
+    records = torch.zeros((steps, 16), dtype=torch.float64, device="cuda")
+    with lf2.System((32, 32, 32), 1, "f64") as s:
+        s.upload(phi0, np.zeros_like(phi0))
+        lf2.lf2_leapfrog_init(s.phi, s.pi, p)
+        lf2.lf2_leapfrog(s.phi, s.pi, p, 2)  # warm-up outside the capture, even count
+        lf2.lf2_field_upload(s.phi, phi0)
+        lf2.lf2_field_upload(s.pi, np.zeros_like(phi0))
+        lf2.lf2_leapfrog_init(s.phi, s.pi, p)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            st = torch.cuda.current_stream()
+            for n in range(steps):
+                lf2.lf2_leapfrog(s.phi, s.pi, p, 1, st)
+                lf2.lf2_energy_device(s.phi, s.pi, p, records[n].data_ptr(), st)
+        g.replay()
+        torch.cuda.synchronize()
+        rec = records.cpu().numpy()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()  # time one more replay (the state moves on; only the timing is used)
+        b.record()
+        torch.cuda.synchronize()
+        us_per_step = a.elapsed_time(b) * 1e3 / steps
+    ophi, opi = ora.evolve(phi0, np.zeros_like(phi0), 0, half_kick=True, **kw)
+    for n in range(steps):
+        ophi, opi = ora.evolve(ophi, opi, 1, **kw)
+        oe = ora.energy(ophi, opi, **kw)
+        assert abs(rec[n, 3] - oe["total"]) <= 1e-12 * abs(oe["total"]), n
+        assert abs(rec[n, 10] - oe["sum_sq"][0]) <= 1e-12 * oe["sum_sq"][0], n
+    print(f"32^3 step + energy, one graph: {us_per_step:.1f} us per step")
+    assert us_per_step < 1000
