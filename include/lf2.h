@@ -232,8 +232,8 @@ lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, d
  * first call for a field; this variant allocates nothing: no cudaMalloc, cudaFree, pinned-host
  * or library allocation.  Its scratch is one fixed array inside the library (608 x 16 + 16
  * doubles, 78 KB) that every GPU which loads the library holds until the process exits.  The
- * reduction's grid is fixed, so every lattice fits; if the scratch needed ever exceeded the
- * array, the call would return LF2_ERR_UNSUPPORTED with a message.  The first call on a device
+ * reduction uses at most 608 blocks whatever the lattice, so every lattice fits; if the scratch
+ * needed ever exceeded the array, the call would return LF2_ERR_UNSUPPORTED with a message.  The first call on a device
  * looks up the array's device address (make it before any stream capture).  All calls share
  * the array: calls whose work overlaps on the GPU (different streams, or several host
  * threads) race and must be serialised by the caller.  Arguments, result and synchronisation

@@ -10,8 +10,8 @@
 // plus sum_x phi_a and sum_x phi_a^2.  The dx^3 volume element is applied by the caller.
 //
 // Two passes with a fixed reduction order, so the result is bitwise reproducible: a
-// grid-stride pass over sites leaves one partial per block (a scratch array of
-// kEnergyBlocks x 8 doubles), then one block sums the partials.  The scratch array lives in
+// grid-stride pass over sites leaves one partial row per block (at most kEnergyBlocks rows of
+// kEnergySlots doubles, one block per 1024 sites), then one block sums the rows.  The scratch array lives in
 // global memory owned by the caller of launch_energy.
 #include <mutex>
 
@@ -101,7 +101,11 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy_final(const double *_
 template <typename R>
 cudaError_t launch_typed(const void *phi, const void *pi, const Geom &g, int ncomp, const CoefE &k, double *partials,
                          double *result, cudaStream_t s) {
-    const int nb = kEnergyBlocks;
+    // One block per 1024 sites up to the fixed maximum: small lattices (the 32^3 run with an
+    // energy every step) reduce in few blocks; the grid depends only on the lattice, so the
+    // result is bitwise reproducible for a given lattice.
+    long long want = (g.sites + 1023) / 1024;
+    const int nb = (int)(want < 1 ? 1 : (want > kEnergyBlocks ? kEnergyBlocks : want));
     switch (ncomp) {
 #define LF2_E(NC) \
     case NC: k_energy<R, NC><<<nb, kEnergyThreads, 0, s>>>((const R *)phi, (const R *)pi, g, k, partials); break;

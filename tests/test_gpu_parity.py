@@ -278,3 +278,41 @@ def test_derivative_matches_oracle(lf2, ora, prec, ncomp, dim):
         else:
             tol = 1e-15 if prec == "f64" else 2e-7
             assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+# ------------------------------------------------------------- degenerate and edge cases
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 5), (2, 1, 3), (1, 7, 1), (4, 1, 1)])
+@pytest.mark.parametrize("prec", ["f64", "f32k"])
+def test_degenerate_lattices(lf2, ora, shape, prec):
+    """Lattices one site thick in some dimension: a site is its own neighbour there, so that
+    dimension's Laplacian term vanishes; the one-site lattice is a single anharmonic oscillator."""
+    nx, ny, nz = shape
+    kw = dict(dx=1.0, dt=0.1, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(nx, ny, nz, 2, sigma=0.5, seed=151)
+    ophi, opi = ora.evolve(phi0, np.zeros_like(phi0), 10, half_kick=True, **kw)
+    oe = ora.energy(ophi, opi, **kw)
+    phi, pi, e = run_gpu(lf2, phi0, np.zeros_like(phi0), 10, prec, kw)
+    tol = F64_TOL if prec == "f64" else 1e-5
+    assert relmax(phi, ophi) <= tol and relmax(pi, opi) <= tol
+    assert abs(e["total"] - oe["total"]) <= tol * abs(oe["total"])
+
+
+def test_zero_steps_is_identity_and_time_reversal(lf2):
+    nx, ny, nz = 24, 16, 12
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi0 = inputs.gaussian_field(nx, ny, nz, 1, sigma=0.3, seed=161)
+    pi_h = inputs.gaussian_field(nx, ny, nz, 1, sigma=0.1, seed=162)
+    p = lf2.params(**kw)
+    back = lf2.params(**dict(kw, dt=-kw["dt"]))
+    with lf2.System((nx, ny, nz), 1, "f64") as s:
+        s.upload(phi0, pi_h)
+        lf2.lf2_leapfrog(s.phi, s.pi, p, 0)
+        a = s.download()
+        assert np.array_equal(a[0], phi0) and np.array_equal(a[1], pi_h)
+        lf2.lf2_leapfrog(s.phi, s.pi, p, 30)
+        # one more kick turns pi_{n-1/2} into pi_{n+1/2}: the start-up half-kick with dt' = -2 dt
+        # is pi - (dt'/2) F = pi + dt F; then 30 steps with -dt retrace the path
+        lf2.lf2_leapfrog_init(s.phi, s.pi, lf2.params(**dict(kw, dt=-2 * kw["dt"])))
+        lf2.lf2_leapfrog(s.phi, s.pi, back, 30)
+        rec = s.download()[0]
+    assert np.max(np.abs(rec - phi0)) <= 1e-12
