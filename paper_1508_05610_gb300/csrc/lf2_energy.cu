@@ -151,8 +151,8 @@ cudaError_t launch_energy_record(const double *result, double vol, double *out, 
 // framework owns the device allocator, or that must not make allocation calls at all.
 // lf2_energy allocates its partial-sum scratch on first use; lf2_energy_noalloc uses this
 // file-scope array instead.  Every GPU that loads the library holds it until process exit.
-// It holds the per-block partials of the reduction's fixed grid plus one result row; the grid
-// does not depend on the lattice, so the capacity is a constant.
+// It holds the per-block partials of the reduction's grid plus one result row; the grid has at
+// most kEnergyBlocks blocks whatever the lattice, so the capacity is a constant.
 static __device__ __align__(256) double g_energy_noalloc[kEnergyNoallocDoubles];
 
 namespace {

@@ -3,8 +3,9 @@
 // An ensemble groups (phi, pi) field pairs of one precision and component count, each on its
 // own lattice and with its own parameters.  lf2_ensemble_run advances all of them by nsteps
 // with one CUDA-graph launch: the graph holds nsteps / depth temporal-blocking passes, each a
-// single persistent kernel launch whose blocks walk a work list of (member, tile, z-chunk)
-// items, longest chunks first, followed by the leftover single steps per member.  Members
+// single persistent kernel launch whose blocks take (member, tile, z-chunk) items, longest
+// chunks first, from a counter zeroed before the pass, followed by the leftover single steps
+// per member.  Members
 // are independent, so no block ever waits for another; the graph is captured once per
 // (nsteps, buffer parities) and relaunched.
 #include <cuda_runtime.h>
@@ -38,6 +39,7 @@ struct lf2_ensemble_s {
     bool tblock = false;  // temporal-blocking passes usable for every member
     int4 *d_items = nullptr;
     int nitems = 0;
+    int *d_counter = nullptr;  // work-list position of the running pass
     cudaStream_t capture = nullptr;
     std::vector<CapturedRun> runs;
 };
@@ -134,7 +136,7 @@ lf2_status enqueue_run(lf2_ensemble e, int nsteps, const TbMember *d_members, cu
     const int depth = e->tblock ? e->cfg.depth : 0;
     const int passes = depth ? nsteps / depth : 0;
     for (int k = 0; k < passes; ++k) {
-        TbEnsembleLaunch L{d_members, e->d_items, e->nitems, k & 1, e->cfg, e->ncomp, e->prec};
+        TbEnsembleLaunch L{d_members, e->d_items, e->nitems, e->d_counter, k & 1, e->cfg, e->ncomp, e->prec};
         cudaError_t err = launch_tblock_ensemble(L, s);
         if (err != cudaSuccess) return cuda_error(err, "ensemble pass");
     }
@@ -215,6 +217,7 @@ lf2_status lf2_ensemble_create(int n, const lf2_field *phis, const lf2_field *pi
     cudaError_t err = cudaSuccess;
     if (st == LF2_OK) err = cudaDeviceSynchronize();
     if (st == LF2_OK && err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->capture, cudaStreamNonBlocking);
+    if (st == LF2_OK && err == cudaSuccess) err = cudaMalloc(&e->d_counter, sizeof(int));
     if (st == LF2_OK && err != cudaSuccess) st = cuda_error(err, "ensemble set-up");
     if (st == LF2_OK) {
         // default configuration: depth 4 with the widest packed columns that fit, else one-step
@@ -231,6 +234,7 @@ lf2_status lf2_ensemble_create(int n, const lf2_field *phis, const lf2_field *pi
     if (st != LF2_OK) {
         if (e->capture) cudaStreamDestroy(e->capture);
         if (e->d_items) cudaFree(e->d_items);
+        if (e->d_counter) cudaFree(e->d_counter);
         delete e;
         return st;
     }
@@ -243,6 +247,7 @@ lf2_status lf2_ensemble_destroy(lf2_ensemble e) {
     if (!e) return set_error(LF2_ERR_INVALID, "ensemble is NULL");
     free_runs(e);
     if (e->d_items) cudaFree(e->d_items);
+    if (e->d_counter) cudaFree(e->d_counter);
     if (e->capture) cudaStreamDestroy(e->capture);
     for (int m = 0; m < e->n; ++m) e->phi[m]->lat->users--;
     delete e;

@@ -320,6 +320,7 @@ struct TbEnsembleLaunch {
     const TbMember *members;  // device
     const int4 *items;        // device: (member, tile x, tile y, z-chunk), longest chunks first
     int nitems;
+    int *counter;             // device: next item, zeroed by the launcher before each pass
     int flip;
     TbConfig c;
     int ncomp;

@@ -340,14 +340,23 @@ __global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>())
                                         blockIdx.y, blockIdx.z);
 }
 
-// Ensemble pass: one launch covers the tiles of every member lattice.  The blocks walk a
-// shared work list (longest chunks first) with a fixed stride, so the assignment is
-// deterministic; members are independent, so no block waits on another.
+// Ensemble pass: one launch covers the tiles of every member lattice, items ordered longest
+// chunk first.  Which block computes an item does not change its result, so the dynamic
+// assignment keeps the output bitwise deterministic.
 template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
 __global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>()))
     k_tblock_ensemble(const TbMember *__restrict__ members, const int4 *__restrict__ items, int nitems, int flip,
-                      int TX, int TY) {
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+                      int TX, int TY, int *__restrict__ counter) {
+    // Each block takes the next item from a shared counter (zeroed before the launch), so the
+    // longest-first work list is scheduled greedily.  The loop ends when the counter passes
+    // the last item; no block waits on another.
+    __shared__ int s_item;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
         const int4 w = items[it];
         const TbMember &m = members[w.x];
         const int f = m.front ^ flip;
@@ -397,7 +406,9 @@ cudaError_t launch_ens_t(const TbEnsembleLaunch &e, cudaStream_t s) {
     int grid = (per_sm > 0 ? per_sm : 1) * sms;
     if (grid > e.nitems) grid = e.nitems;
     if (grid < 1) return cudaSuccess;
-    kern<<<grid, threads, smem, s>>>(e.members, e.items, e.nitems, e.flip, e.c.tile_x, e.c.tile_y);
+    err = cudaMemsetAsync(e.counter, 0, sizeof(int), s);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, threads, smem, s>>>(e.members, e.items, e.nitems, e.flip, e.c.tile_x, e.c.tile_y, e.counter);
     return cudaGetLastError();
 }
 
