@@ -225,12 +225,28 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
  * Calls on one phi field share that scratch: order them on one stream. */
 lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, double *dev_out, void *stream);
 
+/* Advances nsteps exactly as lf2_leapfrog does (bitwise the same fields) and writes, for
+ * k = 0 .. nsteps-1, the energy record of the state at the start of step k (phi_k and the
+ * synchronised pi_k, as lf2_energy defines them) to dev_records + 16 k: nsteps lf2_energy_t
+ * records in device memory, caller-owned.  The paper's programs report diagnostics every step;
+ * here each step is ONE kernel that reads the stencil once for both the energy and the update
+ * (kick and drift), visiting the sites in the order and with the arithmetic of lf2_energy, so
+ * each record is bitwise the one lf2_energy_device gives for that state.  Meant for runs with
+ * an energy every step: the kernel is the one-thread-per-site one, not the tiled kernels of
+ * lf2_leapfrog.  Enqueues on `stream` without waiting; after the first call on phi (which may
+ * allocate its back buffer and energy scratch, so make it outside a stream capture) calls
+ * allocate nothing and can be captured into a CUDA graph.  Calls on one phi share its energy
+ * scratch with lf2_energy and lf2_energy_device: order them on one stream.
+ * LF2_ERR_INVALID for nsteps < 0 or dev_records NULL with nsteps > 0. */
+lf2_status lf2_leapfrog_energy(lf2_field phi, lf2_field pi, const lf2_params *p, int nsteps, double *dev_records,
+                               void *stream);
+
 /* lf2_energy for callers that cannot allocate device memory.  The paper has no counterpart;
  * this entry point exists for callers whose device allocator belongs to someone else (a memory
  * pool or host framework that forbids cudaMalloc while it runs) or that must make no
  * allocation call at all.  lf2_energy allocates scratch and a pinned result buffer on its
  * first call for a field; this variant allocates nothing: no cudaMalloc, cudaFree, pinned-host
- * or library allocation.  Its scratch is one fixed array inside the library (608 x 16 + 16
+ * or library allocation.  Its scratch is one fixed array inside the library (608 x 16 + 17
  * doubles, 78 KB) that every GPU which loads the library holds until the process exits.  The
  * reduction uses at most 608 blocks whatever the lattice, so every lattice fits; if the scratch
  * needed ever exceeded the array, the call would return LF2_ERR_UNSUPPORTED with a message.  The first call on a device

@@ -137,8 +137,14 @@ lf2_status ensure_tblock(lf2_field phi, lf2_field pi, cudaStream_t s) {
 lf2_status ensure_energy_scratch(lf2_field f) {
     if (!f->energy_scratch) {
         void *d = nullptr;
-        LF2_CUDA(cudaMalloc(&d, sizeof(double) * (kEnergyBlocks * kEnergySlots + kEnergySlots)),
-                 "cudaMalloc(energy scratch)");
+        LF2_CUDA(cudaMalloc(&d, sizeof(double) * kEnergyScratchDoubles), "cudaMalloc(energy scratch)");
+        // the finished-block counter must start at zero (each reduction leaves it at zero)
+        const double zero = 0.0;
+        cudaError_t e = cudaMemcpy((double *)d + kEnergyCounterOffset, &zero, sizeof zero, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(e, "energy scratch counter");
+        }
         f->energy_scratch = (double *)d;
     }
     if (!f->energy_host) {
@@ -486,27 +492,14 @@ lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_ener
     st = ensure_energy_scratch(phi);
     if (st != LF2_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    double *partials = phi->energy_scratch;
-    double *result = phi->energy_scratch + kEnergyBlocks * kEnergySlots;
-    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
-                           result, s),
+    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p,
+                           phi->energy_scratch, nullptr, s),
              "energy launch");
-    LF2_CUDA(cudaMemcpyAsync(phi->energy_host, result, kEnergySlots * sizeof(double), cudaMemcpyDeviceToHost, s),
+    LF2_CUDA(cudaMemcpyAsync(phi->energy_host, phi->energy_scratch + kEnergyRecordOffset, sizeof(lf2_energy_t),
+                             cudaMemcpyDeviceToHost, s),
              "energy copy");
     LF2_CUDA(cudaStreamSynchronize(s), "energy sync");
-    const double *r = phi->energy_host;
-    const double vol = p->dx * p->dx * p->dx;
-    lf2_energy_t e;
-    memset(&e, 0, sizeof e);
-    e.kinetic = vol * r[0];
-    e.gradient = vol * r[1];
-    e.potential = vol * r[2];
-    e.total = e.kinetic + e.gradient + e.potential;
-    for (int a = 0; a < phi->ncomp; ++a) {
-        e.sum[a] = r[3 + a];
-        e.sum_sq[a] = r[3 + kMaxComp + a];
-    }
-    *out = e;
+    memcpy(out, phi->energy_host, sizeof(lf2_energy_t));
     return LF2_OK;
 }
 
@@ -517,13 +510,29 @@ lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, d
     if (!dev_out) return fail(LF2_ERR_INVALID, "output pointer is NULL");
     if (!phi->energy_scratch)
         return fail(LF2_ERR_STATE, "no energy scratch yet: call lf2_leapfrog_init or lf2_energy on phi first");
-    cudaStream_t s = (cudaStream_t)stream;
-    double *partials = phi->energy_scratch;
-    double *result = phi->energy_scratch + kEnergyBlocks * kEnergySlots;
     LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p,
-                           partials, result, s),
+                           phi->energy_scratch, dev_out, (cudaStream_t)stream),
              "energy launch");
-    LF2_CUDA(launch_energy_record(result, p->dx * p->dx * p->dx, dev_out, s), "energy record");
+    return LF2_OK;
+}
+
+lf2_status lf2_leapfrog_energy(lf2_field phi, lf2_field pi, const lf2_params *p, int nsteps, double *dev_records,
+                               void *stream) {
+    lf2_status st = check_pair(phi, pi);
+    if (st == LF2_OK) st = check_params(p);
+    if (st != LF2_OK) return st;
+    if (nsteps < 0) return fail(LF2_ERR_INVALID, "nsteps must be >= 0");
+    if (nsteps > 0 && !dev_records) return fail(LF2_ERR_INVALID, "records pointer is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = ensure_dynamic(phi, s);
+    if (st == LF2_OK) st = ensure_energy_scratch(phi);
+    if (st != LF2_OK) return st;
+    for (int k = 0; k < nsteps; ++k) {
+        const StepArgs a = step_args(phi, pi, p, p->dt, true);
+        LF2_CUDA(launch_step_energy(a, phi->energy_scratch, dev_records + (size_t)k * kEnergySlots, s),
+                 "step+energy launch");
+        phi->front = 1 - phi->front;
+    }
     return LF2_OK;
 }
 
@@ -532,36 +541,18 @@ lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, 
     if (st == LF2_OK) st = check_params(p);
     if (st != LF2_OK) return st;
     if (!out) return fail(LF2_ERR_INVALID, "output pointer is NULL");
-    // The reduction writes one partial row per block of its fixed grid, then one result row.
-    const long long needed = (long long)kEnergyBlocks * kEnergySlots + kEnergySlots;
-    if (needed > kEnergyNoallocDoubles)
-        return fail(LF2_ERR_UNSUPPORTED, "energy reduction needs %lld scratch doubles, the fixed array holds %d",
-                    needed, kEnergyNoallocDoubles);
     double *scratch = nullptr;
     LF2_CUDA(energy_noalloc_scratch(&scratch), "cudaGetSymbolAddress(energy scratch)");
     cudaStream_t s = (cudaStream_t)stream;
-    double *partials = scratch;
-    double *result = scratch + kEnergyBlocks * kEnergySlots;
-    // Every slot read below is written earlier in the same call, so nothing left over from a
-    // previous call is used and nothing needs clearing.
-    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p, partials,
-                           result, s),
+    // The reduction writes every partial row and the record it reads back, and leaves the
+    // finished-block counter at zero (where the zero-initialised array starts it).
+    LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p,
+                           scratch, nullptr, s),
              "energy launch");
     double r[kEnergySlots];
-    LF2_CUDA(cudaMemcpyAsync(r, result, sizeof r, cudaMemcpyDeviceToHost, s), "energy copy");
+    LF2_CUDA(cudaMemcpyAsync(r, scratch + kEnergyRecordOffset, sizeof r, cudaMemcpyDeviceToHost, s), "energy copy");
     LF2_CUDA(cudaStreamSynchronize(s), "energy sync");
-    const double vol = p->dx * p->dx * p->dx;
-    lf2_energy_t e;
-    memset(&e, 0, sizeof e);
-    e.kinetic = vol * r[0];
-    e.gradient = vol * r[1];
-    e.potential = vol * r[2];
-    e.total = e.kinetic + e.gradient + e.potential;
-    for (int a = 0; a < phi->ncomp; ++a) {
-        e.sum[a] = r[3 + a];
-        e.sum_sq[a] = r[3 + kMaxComp + a];
-    }
-    *out = e;
+    memcpy(out, r, sizeof(lf2_energy_t));
     return LF2_OK;
 }
 

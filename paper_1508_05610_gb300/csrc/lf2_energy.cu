@@ -1,18 +1,23 @@
-// lf2_energy.cu -- FP64 energy and checksum reduction (all precisions).
+// lf2_energy.cu -- FP64 energy and checksum reduction (all precisions), alone or fused into a
+// leapfrog step.
 //
 // Energy at integer step n from phi_n and pi_{n-1/2}:
-//   pi_n       = pi_{n-1/2} + (dt/2) F(phi_n)          (synchronised momentum)
+//   pi_n       = pi_{n-1/2} + (dt/2) F(phi_n)          (synchronised momentum: a half kick)
 //   kinetic    = sum_x 1/2 sum_a pi_{a,n}^2
 //   gradient   = sum_x sum_a sum_i (phi_a(x+i) - phi_a(x))^2 / (2 dx^2)
 //                (forward differences: the discrete gradient energy whose variation is the
 //                 7-point Laplacian built from the Site neighbours x+i, x-i of Sec. 3.4)
 //   potential  = sum_x [lambda/4 (|phi|^2 - eta^2)^2 + m2/2 |phi|^2]
-// plus sum_x phi_a and sum_x phi_a^2.  The dx^3 volume element is applied by the caller.
+// plus sum_x phi_a and sum_x phi_a^2, all times the volume element dx^3 except the sums.
 //
-// Two passes with a fixed reduction order, so the result is bitwise reproducible: a
-// grid-stride pass over sites leaves one partial row per block (at most kEnergyBlocks rows of
-// kEnergySlots doubles, one block per 1024 sites), then one block sums the rows.  The scratch array lives in
-// global memory owned by the caller of launch_energy.
+// Each site adds raw sums (pi_n^2, squared differences, (|phi|^2 - eta^2)^2, phi_a, phi_a^2)
+// to per-thread FP64 accumulators; the constant factors are applied once to the totals
+// (the potential's mass term is m2/2 times the sum of the phi_a^2 totals).  A grid-stride
+// pass over sites leaves one partial row per block; the last block to finish (counted with
+// an atomic) sums the rows in block order and writes the record.  The grid depends only on
+// the lattice and every sum has a fixed order, so the result is bitwise reproducible, and the
+// fused step kernels, which visit the sites in the same order with the same per-site
+// arithmetic, give bitwise the record of the stand-alone reduction.
 #include <mutex>
 
 #include "lf2_internal.cuh"
@@ -20,7 +25,12 @@
 namespace lf2 {
 namespace {
 
-constexpr int kSlots = kEnergySlots;
+// Raw sums per thread for NC components: 0 kinetic, 1 gradient, 2 potential, then sum_x phi_a
+// (3 + a) and sum_x phi_a^2 (3 + NC + a).  Partial rows in the scratch keep kEnergySlots
+// doubles of which the first kNs<NC> are used.
+template <int NC>
+constexpr int kNs = 3 + 2 * NC;
+constexpr int kKin = 0, kGrad = 1, kPot = 2, kSum = 3;
 
 template <typename R, int NC>
 __device__ __forceinline__ void load_d(const R *__restrict__ f, long long s, double (&v)[NC]) {
@@ -28,132 +38,292 @@ __device__ __forceinline__ void load_d(const R *__restrict__ f, long long s, dou
     for (int a = 0; a < NC; ++a) v[a] = (double)__ldg(f + s * NC + a);
 }
 
-__device__ __forceinline__ void block_reduce_store(double (&acc)[kSlots], double *__restrict__ dst) {
-    __shared__ double sh[kSlots][kEnergyThreads];
+// Adds one site's raw sums to acc.  c: phi_n at the site, xm..zp: its neighbours in the order
+// -x, +x, -y, +y, -z, +z; p: pi_{n-1/2}.  Explicit round-to-nearest operations keep the
+// stand-alone and fused kernels bitwise equal; the half kick is the FP64 kick's arithmetic.
+template <int NC>
+__device__ __forceinline__ void energy_site(const double (&c)[NC], const double (&xm)[NC], const double (&xp)[NC],
+                                            const double (&ym)[NC], const double (&yp)[NC], const double (&zm)[NC],
+                                            const double (&zp)[NC], const double (&p)[NC], double (&acc)[kNs<NC>],
+                                            const CoefE &k) {
+    double s2 = __dmul_rn(c[0], c[0]);
 #pragma unroll
-    for (int j = 0; j < kSlots; ++j) sh[j][threadIdx.x] = acc[j];
+    for (int b = 1; b < NC; ++b) s2 = __fma_rn(c[b], c[b], s2);
+    const double gh = __fma_rn(k.hl, s2, k.hb0);
+    const double w = __dsub_rn(s2, k.eta2);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        const double nb = __dadd_rn(__dadd_rn(xm[a], xp[a]), __dadd_rn(__dadd_rn(ym[a], yp[a]), __dadd_rn(zm[a], zp[a])));
+        const double pin = __fma_rn(k.ah, nb, __fma_rn(-gh, c[a], p[a]));
+        acc[kKin] = __fma_rn(pin, pin, acc[kKin]);
+        const double ex = __dsub_rn(xp[a], c[a]), ey = __dsub_rn(yp[a], c[a]), ez = __dsub_rn(zp[a], c[a]);
+        acc[kGrad] = __fma_rn(ez, ez, __fma_rn(ey, ey, __fma_rn(ex, ex, acc[kGrad])));
+        acc[kSum + a] = __dadd_rn(acc[kSum + a], c[a]);
+        acc[kSum + NC + a] = __fma_rn(c[a], c[a], acc[kSum + NC + a]);
+    }
+    acc[kPot] = __fma_rn(w, w, acc[kPot]);
+}
+
+// Block sum of acc, left in sh[j][0].  A pairwise tree whose additions at each level are packed
+// onto consecutive threads: an FP64 warp instruction costs the same however few of its lanes
+// are active, so the levels with fewer than 32 pairs per sum still fill whole warps.
+template <int NS>
+__device__ __forceinline__ void block_sum(const double (&acc)[NS], double (&sh)[NS][kEnergyThreads]) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j) sh[j][threadIdx.x] = acc[j];
     __syncthreads();
-    for (int w = kEnergyThreads / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) {
 #pragma unroll
-            for (int j = 0; j < kSlots; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + w];
+    for (int w = kEnergyThreads / 2; w > 0; w >>= 1) {
+        for (int t = threadIdx.x; t < NS * w; t += kEnergyThreads) {
+            const int j = t / w, i = t % w;
+            sh[j][i] = __dadd_rn(sh[j][i], sh[j][i + w]);
         }
         __syncthreads();
     }
-    if (threadIdx.x < kSlots) dst[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// End of every energy kernel: stores this block's partial row, and the last block to get here
+// sums all rows (in block order) and writes the record.  No block waits for another.
+template <int NC>
+__device__ __forceinline__ void finish_energy(const double (&acc)[kNs<NC>], double (&sh)[kNs<NC>][kEnergyThreads],
+                                              double *__restrict__ scratch, const CoefE &k,
+                                              double *__restrict__ record) {
+    constexpr int NS = kNs<NC>;
+    __shared__ bool s_last;
+    block_sum<NS>(acc, sh);
+    if (threadIdx.x < NS) scratch[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+    __threadfence();  // this block's row is visible device-wide before the block is counted
+    __syncthreads();
+    unsigned int *counter = reinterpret_cast<unsigned int *>(scratch + kEnergyCounterOffset);
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();  // every other block's row is visible to this one
+    double tot[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) tot[j] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) tot[j] = __dadd_rn(tot[j], __ldcg(scratch + (size_t)b * kEnergySlots + j));
+    }
+    block_sum<NS>(tot, sh);
+    if (threadIdx.x == 0) {
+        double r[kEnergySlots];
+        double ssq = 0.0;
+        for (int a = 0; a < NC; ++a) ssq += sh[kSum + NC + a][0];
+        r[0] = k.vol * (0.5 * sh[kKin][0]);
+        r[1] = k.vol * (0.5 * k.inv_dx2 * sh[kGrad][0]);
+        r[2] = k.vol * (0.25 * k.lam * sh[kPot][0] + 0.5 * k.m2 * ssq);
+        r[3] = r[0] + r[1] + r[2];
+        for (int a = 0; a < kMaxComp; ++a) {
+            r[4 + a] = a < NC ? sh[kSum + a][0] : 0.0;
+            r[4 + kMaxComp + a] = a < NC ? sh[kSum + NC + a][0] : 0.0;
+        }
+        double *own = scratch + kEnergyRecordOffset;
+        for (int j = 0; j < kEnergySlots; ++j) {
+            own[j] = r[j];
+            if (record) record[j] = r[j];
+        }
+        *counter = 0u;  // ready for the next launch on this scratch
+    }
+}
+
+// Linear indices of the six periodic neighbours of site s.
+struct Nbr {
+    long long xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ Nbr neighbours(long long s, const Geom &g) {
+    const int x = (int)(s % g.nx);
+    const long long r = s / g.nx;
+    const int y = (int)(r % g.ny);
+    const int z = (int)(r / g.ny);
+    const long long row = g.nx, plane = (long long)g.nx * g.ny;
+    return Nbr{s - x + wrap_dn(x, g.nx),       s - x + wrap_up(x, g.nx),       s + (wrap_dn(y, g.ny) - y) * row,
+               s + (wrap_up(y, g.ny) - y) * row, s + (wrap_dn(z, g.nz) - z) * plane, s + (wrap_up(z, g.nz) - z) * plane};
 }
 
 template <typename R, int NC>
 __global__ void __launch_bounds__(kEnergyThreads) k_energy(const R *__restrict__ phi, const R *__restrict__ pi, Geom g,
-                                                           CoefE k, double *__restrict__ partials) {
-    double acc[kSlots];
+                                                           CoefE k, double *__restrict__ scratch, double *__restrict__ record) {
+    __shared__ double sh[kNs<NC>][kEnergyThreads];
+    double acc[kNs<NC>];
 #pragma unroll
-    for (int j = 0; j < kSlots; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kNs<NC>; ++j) acc[j] = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long row = g.nx, plane = (long long)g.nx * g.ny;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride) {
-        const int x = (int)(s % g.nx);
-        const long long r = s / g.nx;
-        const int y = (int)(r % g.ny);
-        const int z = (int)(r / g.ny);
+        const Nbr n = neighbours(s, g);
         double c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC];
         load_d<R, NC>(phi, s, c);
-        load_d<R, NC>(phi, s - x + wrap_dn(x, g.nx), xm);
-        load_d<R, NC>(phi, s - x + wrap_up(x, g.nx), xp);
-        load_d<R, NC>(phi, s + (wrap_dn(y, g.ny) - y) * row, ym);
-        load_d<R, NC>(phi, s + (wrap_up(y, g.ny) - y) * row, yp);
-        load_d<R, NC>(phi, s + (wrap_dn(z, g.nz) - z) * plane, zm);
-        load_d<R, NC>(phi, s + (wrap_up(z, g.nz) - z) * plane, zp);
+        load_d<R, NC>(phi, n.xm, xm);
+        load_d<R, NC>(phi, n.xp, xp);
+        load_d<R, NC>(phi, n.ym, ym);
+        load_d<R, NC>(phi, n.yp, yp);
+        load_d<R, NC>(phi, n.zm, zm);
+        load_d<R, NC>(phi, n.zp, zp);
         load_d<R, NC>(pi, s, p);
-        double s2 = 0.0;
-#pragma unroll
-        for (int a = 0; a < NC; ++a) s2 += c[a] * c[a];
-        const double w = s2 - k.eta2;
-        const double gpot = k.lam * w + k.m2;
-#pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            const double nb = ((xm[a] + xp[a]) + (ym[a] + yp[a])) + (zm[a] + zp[a]);
-            const double F = (nb - 6.0 * c[a]) * k.inv_dx2 - gpot * c[a];
-            const double pin = p[a] + k.half_dt * F;
-            acc[0] += 0.5 * pin * pin;
-            const double ex = xp[a] - c[a], ey = yp[a] - c[a], ez = zp[a] - c[a];
-            acc[1] += 0.5 * k.inv_dx2 * ((ex * ex + ey * ey) + ez * ez);
-            acc[3 + a] += c[a];
-            acc[3 + kMaxComp + a] += c[a] * c[a];
-        }
-        acc[2] += 0.25 * k.lam * w * w + 0.5 * k.m2 * s2;
+        energy_site<NC>(c, xm, xp, ym, yp, zm, zp, p, acc, k);
     }
-    block_reduce_store(acc, partials + (size_t)blockIdx.x * kSlots);
+    finish_energy<NC>(acc, sh, scratch, k, record);
 }
 
-__global__ void __launch_bounds__(kEnergyThreads) k_energy_final(const double *__restrict__ partials, int nblocks,
-                                                                 double *__restrict__ result) {
-    double acc[kSlots];
+// Fused step + energy, FP64: the energy of (phi_n, pi_{n-1/2}) and the step to
+// (phi_{n+1}, pi_{n+1/2}) from one read of each site's stencil.
+template <int NC>
+__global__ void __launch_bounds__(kEnergyThreads)
+    k_step_energy_f64(const double *__restrict__ phi, double *__restrict__ phi_out, double *__restrict__ pi, Geom g,
+                      Coef64 k, CoefE ke, double *__restrict__ scratch, double *__restrict__ record) {
+    __shared__ double sh[kNs<NC>][kEnergyThreads];
+    double acc[kNs<NC>];
 #pragma unroll
-    for (int j = 0; j < kSlots; ++j) acc[j] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    for (int j = 0; j < kNs<NC>; ++j) acc[j] = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride) {
+        const Nbr n = neighbours(s, g);
+        double c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], out[NC];
+        load_d<double, NC>(phi, s, c);
+        load_d<double, NC>(phi, n.xm, xm);
+        load_d<double, NC>(phi, n.xp, xp);
+        load_d<double, NC>(phi, n.ym, ym);
+        load_d<double, NC>(phi, n.yp, yp);
+        load_d<double, NC>(phi, n.zm, zm);
+        load_d<double, NC>(phi, n.zp, zp);
 #pragma unroll
-        for (int j = 0; j < kSlots; ++j) acc[j] += partials[(size_t)b * kSlots + j];
+        for (int a = 0; a < NC; ++a) p[a] = pi[s * NC + a];
+        energy_site<NC>(c, xm, xp, ym, yp, zm, zp, p, acc, ke);
+        update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, out, k);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            pi[s * NC + a] = p[a];
+            phi_out[s * NC + a] = out[a];
+        }
     }
-    block_reduce_store(acc, result);
+    finish_energy<NC>(acc, sh, scratch, ke, record);
+}
+
+// Fused step + energy, FP32 storage (KAHAN: compensated drift); the energy is computed in FP64
+// from the exact conversions of the stored values.
+template <int NC, bool KAHAN>
+__global__ void __launch_bounds__(kEnergyThreads)
+    k_step_energy_f32(const float *__restrict__ phi, float *__restrict__ phi_out, float *__restrict__ pi,
+                      float *__restrict__ comp, Geom g, Coef32 k, CoefE ke, double *__restrict__ scratch,
+                      double *__restrict__ record) {
+    __shared__ double sh[kNs<NC>][kEnergyThreads];
+    double acc[kNs<NC>];
+#pragma unroll
+    for (int j = 0; j < kNs<NC>; ++j) acc[j] = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride) {
+        const Nbr n = neighbours(s, g);
+        float c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], out[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            c[a] = __ldg(phi + s * NC + a);
+            xm[a] = __ldg(phi + n.xm * NC + a);
+            xp[a] = __ldg(phi + n.xp * NC + a);
+            ym[a] = __ldg(phi + n.ym * NC + a);
+            yp[a] = __ldg(phi + n.yp * NC + a);
+            zm[a] = __ldg(phi + n.zm * NC + a);
+            zp[a] = __ldg(phi + n.zp * NC + a);
+            p[a] = pi[s * NC + a];
+            cm[a] = KAHAN ? comp[s * NC + a] : 0.0f;
+        }
+        double dc[NC], dxm[NC], dxp[NC], dym[NC], dyp[NC], dzm[NC], dzp[NC], dp[NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            dc[a] = c[a];
+            dxm[a] = xm[a];
+            dxp[a] = xp[a];
+            dym[a] = ym[a];
+            dyp[a] = yp[a];
+            dzm[a] = zm[a];
+            dzp[a] = zp[a];
+            dp[a] = p[a];
+        }
+        energy_site<NC>(dc, dxm, dxp, dym, dyp, dzm, dzp, dp, acc, ke);
+        update_f32<NC, KAHAN>(c, xm, xp, ym, yp, zm, zp, p, cm, out, k);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            pi[s * NC + a] = p[a];
+            phi_out[s * NC + a] = out[a];
+            if (KAHAN) comp[s * NC + a] = cm[a];
+        }
+    }
+    finish_energy<NC>(acc, sh, scratch, ke, record);
+}
+
+// One block per 256 sites up to kEnergyBlocks: small lattices (a 32^3 run with an energy every
+// step) spread over many SMs, large ones keep at most kEnergyBlocks partial rows.
+int energy_grid(long long sites) {
+    const long long want = (sites + kEnergyThreads - 1) / kEnergyThreads;
+    return (int)(want < 1 ? 1 : (want > kEnergyBlocks ? kEnergyBlocks : want));
 }
 
 template <typename R>
-cudaError_t launch_typed(const void *phi, const void *pi, const Geom &g, int ncomp, const CoefE &k, double *partials,
-                         double *result, cudaStream_t s) {
-    // One block per 1024 sites up to the fixed maximum: small lattices (the 32^3 run with an
-    // energy every step) reduce in few blocks; the grid depends only on the lattice, so the
-    // result is bitwise reproducible for a given lattice.
-    long long want = (g.sites + 1023) / 1024;
-    const int nb = (int)(want < 1 ? 1 : (want > kEnergyBlocks ? kEnergyBlocks : want));
+cudaError_t launch_typed(const void *phi, const void *pi, const Geom &g, int ncomp, const CoefE &k, double *scratch,
+                         double *record, cudaStream_t s) {
+    const int nb = energy_grid(g.sites);
     switch (ncomp) {
-#define LF2_E(NC) \
-    case NC: k_energy<R, NC><<<nb, kEnergyThreads, 0, s>>>((const R *)phi, (const R *)pi, g, k, partials); break;
+#define LF2_E(NC)                                                                                               \
+    case NC:                                                                                                    \
+        k_energy<R, NC><<<nb, kEnergyThreads, 0, s>>>((const R *)phi, (const R *)pi, g, k, scratch, record); \
+        break;
         LF2_E(1) LF2_E(2) LF2_E(3) LF2_E(4) LF2_E(5) LF2_E(6)
 #undef LF2_E
         default: return cudaErrorInvalidValue;
     }
-    k_energy_final<<<1, kEnergyThreads, 0, s>>>(partials, nb, result);
     return cudaGetLastError();
+}
+
+template <int NC>
+void step_energy_nc(const StepArgs &a, const CoefE &ke, int nb, double *scratch, double *record, cudaStream_t s) {
+    if (a.prec == LF2_F64) {
+        k_step_energy_f64<NC><<<nb, kEnergyThreads, 0, s>>>((const double *)a.phi, (double *)a.phi_out, (double *)a.pi,
+                                                            a.g, make_coef64(a.p, a.dt), ke, scratch, record);
+        return;
+    }
+    const Coef32 k = make_coef32(a.p, a.dt);
+    if (a.prec == LF2_F32_KAHAN)
+        k_step_energy_f32<NC, true><<<nb, kEnergyThreads, 0, s>>>((const float *)a.phi, (float *)a.phi_out,
+                                                                  (float *)a.pi, a.comp, a.g, k, ke, scratch, record);
+    else
+        k_step_energy_f32<NC, false><<<nb, kEnergyThreads, 0, s>>>((const float *)a.phi, (float *)a.phi_out,
+                                                                   (float *)a.pi, a.comp, a.g, k, ke, scratch, record);
 }
 
 }  // namespace
 
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
-                          const lf2_params &p, double *partials, double *result, cudaStream_t s) {
+                          const lf2_params &p, double *scratch, double *record, cudaStream_t s) {
     const CoefE k = make_coefE(p);
-    if (prec == LF2_F64) return launch_typed<double>(phi, pi, g, ncomp, k, partials, result, s);
-    return launch_typed<float>(phi, pi, g, ncomp, k, partials, result, s);
+    if (prec == LF2_F64) return launch_typed<double>(phi, pi, g, ncomp, k, scratch, record, s);
+    return launch_typed<float>(phi, pi, g, ncomp, k, scratch, record, s);
 }
 
-// ------------------------------------------------------ device-side energy record
-// Turns the raw result row into an lf2_energy_t-shaped record in device memory: kinetic,
-// gradient, potential (times dx^3), total, sum[kMaxComp], sum_sq[kMaxComp].
-__global__ void k_energy_record(const double *__restrict__ r, double vol, double *__restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    out[0] = vol * r[0];
-    out[1] = vol * r[1];
-    out[2] = vol * r[2];
-    out[3] = out[0] + out[1] + out[2];
-    for (int a = 0; a < kMaxComp; ++a) {
-        out[4 + a] = r[3 + a];
-        out[4 + kMaxComp + a] = r[3 + kMaxComp + a];
+cudaError_t launch_step_energy(const StepArgs &a, double *scratch, double *record, cudaStream_t s) {
+    if (!a.drift) return cudaErrorInvalidValue;
+    const CoefE ke = make_coefE(a.p);
+    const int nb = energy_grid(a.g.sites);
+    switch (a.ncomp) {
+        case 1: step_energy_nc<1>(a, ke, nb, scratch, record, s); break;
+        case 2: step_energy_nc<2>(a, ke, nb, scratch, record, s); break;
+        case 3: step_energy_nc<3>(a, ke, nb, scratch, record, s); break;
+        case 4: step_energy_nc<4>(a, ke, nb, scratch, record, s); break;
+        case 5: step_energy_nc<5>(a, ke, nb, scratch, record, s); break;
+        case 6: step_energy_nc<6>(a, ke, nb, scratch, record, s); break;
+        default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_energy_record(const double *result, double vol, double *out, cudaStream_t s) {
-    k_energy_record<<<1, 32, 0, s>>>(result, vol, out);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------- fixed scratch for lf2_energy_noalloc
 // Some callers cannot allocate device memory: code that runs while a memory pool or another
 // framework owns the device allocator, or that must not make allocation calls at all.
-// lf2_energy allocates its partial-sum scratch on first use; lf2_energy_noalloc uses this
-// file-scope array instead.  Every GPU that loads the library holds it until process exit.
-// It holds the per-block partials of the reduction's grid plus one result row; the grid has at
-// most kEnergyBlocks blocks whatever the lattice, so the capacity is a constant.
-static __device__ __align__(256) double g_energy_noalloc[kEnergyNoallocDoubles];
+// lf2_energy allocates its scratch on first use; lf2_energy_noalloc uses this file-scope array
+// instead.  Every GPU that loads the library holds it until process exit.  Its size is fixed
+// because the reduction grid has at most kEnergyBlocks blocks whatever the lattice; static
+// device memory starts zeroed, so the finished-block counter starts at zero as required.
+static __device__ __align__(256) double g_energy_noalloc[kEnergyScratchDoubles];
 
 namespace {
 constexpr int kMaxDevices = 64;

@@ -27,8 +27,8 @@ struct lf2_field_s {
     float *comp[2] = {nullptr, nullptr};  // Kahan compensation of phi (F32_KAHAN); comp[cfront] current
     bool own_comp[2] = {false, false};
     int cfront = 0;
-    double *energy_scratch = nullptr;  // kEnergyBlocks*8 partials + 8 results (device)
-    double *energy_host = nullptr;     // 8 pinned doubles
+    double *energy_scratch = nullptr;  // kEnergyScratchDoubles: partial rows, record, counter (device)
+    double *energy_host = nullptr;     // one pinned lf2_energy_t
 };
 
 namespace lf2 {

@@ -33,9 +33,12 @@ struct Coef32 {
     float zero;  // always 0: a run-time zero for the packed path (see make_coef32x2)
 };
 
-// Energy (always FP64).
+// Energy (always FP64).  The synchronised momentum pi_n = pi_{n-1/2} + (dt/2) F(phi_n) is a
+// kick of half a step, folded as in Coef64 with dt/2: ah = (dt/2)/dx^2, hl = (dt/2) lambda,
+// hb0 = (dt/2)(6/dx^2 + m2 - lambda eta^2).  The remaining members scale the raw sums.
 struct CoefE {
-    double inv_dx2, lam, eta2, m2, half_dt;
+    double ah, hl, hb0, eta2;
+    double inv_dx2, lam, m2, vol;  // vol = dx^3
 };
 
 inline Coef64 make_coef64(const lf2_params &p, double dt) {
@@ -48,7 +51,9 @@ inline Coef32 make_coef32(const lf2_params &p, double dt) {
 }
 
 inline CoefE make_coefE(const lf2_params &p) {
-    return CoefE{1.0 / (p.dx * p.dx), p.lambda, p.eta * p.eta, p.m2, 0.5 * p.dt};
+    const double inv_dx2 = 1.0 / (p.dx * p.dx), h = 0.5 * p.dt;
+    return CoefE{h * inv_dx2, h * p.lambda, h * (6.0 * inv_dx2 + p.m2 - p.lambda * p.eta * p.eta), p.eta * p.eta,
+                 inv_dx2,     p.lambda,     p.m2,                                                   p.dx * p.dx * p.dx};
 }
 
 // ------------------------------------------------------------------ per-site update
@@ -274,15 +279,24 @@ cudaError_t launch_site_step(const StepArgs &a, cudaStream_t s);
 bool stream_supported(const StepArgs &a, int tile_y, int zchunk);
 cudaError_t launch_stream_step(const StepArgs &a, int tile_y, int zchunk, int nsteps_hint, cudaStream_t s);
 
-// Energy: writes kEnergySlots doubles to `result` (device): kin, grad, pot (without dx^3),
-// sum[a] at 3 + a, sum_sq[a] at 3 + kMaxComp + a.  `partials` holds kEnergyBlocks x
-// kEnergySlots doubles.
+// Energy reduction scratch (device, kEnergyScratchDoubles doubles): one partial row of
+// kEnergySlots per block, then the record row (an lf2_energy_t), then an unsigned counter of
+// finished blocks that must be zero before the first launch (every launch leaves it zero).
 constexpr int kEnergyBlocks = 152 * 4;
 constexpr int kEnergyThreads = 256;
 constexpr int kEnergySlots = 16;
+constexpr int kEnergyRecordOffset = kEnergyBlocks * kEnergySlots;
+constexpr int kEnergyCounterOffset = kEnergyRecordOffset + kEnergySlots;
+constexpr int kEnergyScratchDoubles = kEnergyCounterOffset + 1;
 static_assert(3 + 2 * kMaxComp <= kEnergySlots, "energy slots");
+// Energy of (phi, pi) as an lf2_energy_t record: written to scratch + kEnergyRecordOffset and,
+// when `record` is not NULL, also to `record` (device).  One launch.
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
-                          const lf2_params &p, double *partials, double *result, cudaStream_t s);
+                          const lf2_params &p, double *scratch, double *record, cudaStream_t s);
+// One leapfrog step (kick + drift, as launch_site_step) that also writes the energy record of
+// the state it starts from to `record`, with the site order and reduction of launch_energy, so
+// the record is bitwise the one launch_energy gives for that state.  One launch.
+cudaError_t launch_step_energy(const StepArgs &a, double *scratch, double *record, cudaStream_t s);
 
 // Temporal blocking: `depth` fused steps per pass over x-y tiles of tile_x x tile_y output
 // sites (plus a depth-site halo), z-chunks of `zchunk` planes.  Unlike the one-step kernels it
@@ -333,11 +347,9 @@ bool tblock_supported(const TbArgs &a, TbConfig &c);
 cudaError_t launch_tblock(const TbArgs &a, const TbConfig &c, cudaStream_t s);
 
 // Writes an lf2_energy_t-shaped record (16 doubles) from a result row to device memory.
-cudaError_t launch_energy_record(const double *result, double vol, double *out, cudaStream_t s);
-static_assert(sizeof(lf2_energy_t) == (4 + 2 * kMaxComp) * sizeof(double), "energy record layout");
+static_assert(sizeof(lf2_energy_t) == kEnergySlots * sizeof(double), "energy record layout");
 
-// Fixed-size scratch of lf2_energy_noalloc: the partials plus one result row (78 KB).
-constexpr int kEnergyNoallocDoubles = kEnergyBlocks * kEnergySlots + kEnergySlots;
+// Fixed-size scratch of lf2_energy_noalloc (kEnergyScratchDoubles doubles, 78 KB).
 cudaError_t energy_noalloc_scratch(double **out);
 
 // Conversions between host-side doubles and storage precision.

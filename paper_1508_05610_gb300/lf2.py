@@ -79,6 +79,7 @@ SIGNATURES = {
     "lf2_energy": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
     "lf2_energy_device": [_vp, _vp, ctypes.POINTER(lf2_params), _vp, _vp],
     "lf2_energy_noalloc": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
+    "lf2_leapfrog_energy": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, _vp, _vp],
     "lf2_ensemble_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(lf2_params),
                             ctypes.POINTER(_vp)],
     "lf2_ensemble_run": [_vp, ctypes.c_int, _vp],
@@ -230,6 +231,12 @@ def lf2_energy(phi, pi, p: lf2_params, stream=None, ncomp=2) -> dict:
 def lf2_energy_device(phi, pi, p: lf2_params, dev_out_ptr, stream=None):
     """Enqueues the energy reduction; writes an lf2_energy_t record to device memory."""
     _call("lf2_energy_device", phi, pi, ctypes.byref(p), dev_out_ptr, _stream_ptr(stream))
+
+
+def lf2_leapfrog_energy(phi, pi, p: lf2_params, nsteps, dev_records_ptr, stream=None):
+    """nsteps leapfrog steps, one kernel each, that also write the energy record of the state at
+    the start of every step (nsteps x 16 doubles of device memory at dev_records_ptr)."""
+    _call("lf2_leapfrog_energy", phi, pi, ctypes.byref(p), int(nsteps), dev_records_ptr, _stream_ptr(stream))
 
 
 ENERGY_RECORD_FIELDS = ["kinetic", "gradient", "potential", "total"] + [f"sum{a}" for a in range(6)] + \
