@@ -27,8 +27,9 @@ def main(argv=None):
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=8)
-    ap.add_argument("--op", default="leapfrog", choices=["leapfrog", "derivative"],
-                    help="derivative: time lf2_field_derivative along --dim instead of leapfrog steps")
+    ap.add_argument("--op", default="leapfrog", choices=["leapfrog", "derivative", "energy", "step_energy"],
+                    help="derivative: time lf2_field_derivative along --dim; energy: time lf2_energy_device; "
+                         "step_energy: time lf2_leapfrog_energy (a step with its energy record per launch)")
     ap.add_argument("--dim", type=int, default=0)
     args = ap.parse_args(argv)
 
@@ -73,6 +74,32 @@ def main(argv=None):
         nbytes = 2 * phi.numel() * phi.element_size()  # read src once, write dst once
         print(json.dumps({"op": "derivative", "lattice": [nx, ny, nz], "ncomp": args.ncomp, "prec": args.prec,
                           "dim": args.dim, "seconds_per_call": t, "algorithmic_GBps": nbytes / t / 1e9}))
+        return
+    if args.op in ("energy", "step_energy"):
+        rec = torch.zeros((max(args.steps, args.warmup, 1), 16), dtype=torch.float64, device=phi.device)
+        try:
+            lf2.lf2_leapfrog_init(fphi, fpi, p, stream)
+
+            def run(count):
+                if args.op == "energy":
+                    for j in range(count):
+                        lf2.lf2_energy_device(fphi, fpi, p, rec[j].data_ptr(), stream)
+                else:
+                    lf2.lf2_leapfrog_energy(fphi, fpi, p, count, rec.data_ptr(), stream)
+            run(args.warmup)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run(args.steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3 / args.steps
+        finally:
+            lf2.lf2_field_free(fphi)
+            lf2.lf2_field_free(fpi)
+            lf2.lf2_lattice_destroy(lat)
+        print(json.dumps({"op": args.op, "lattice": [nx, ny, nz], "ncomp": args.ncomp, "prec": args.prec,
+                          "seconds_per_call": t, "gsu_per_s": nx * ny * nz / t / 1e9}))
         return
     try:
         lf2.lf2_leapfrog_init(fphi, fpi, p, stream)
