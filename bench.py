@@ -278,12 +278,12 @@ def run_gpu(args):
         done = n
         e64 = lf2.lf2_energy(pairs["f64"].fphi, pairs["f64"].fpi, p, stream)
         e32 = lf2.lf2_energy(pairs["f32k"].fphi, pairs["f32k"].fpi, p, stream)
-        a, b = pairs["f32k"].front().double(), pairs["f64"].front()
-        pa, pb = pairs["f32k"].pi_front().double(), pairs["f64"].pi_front()
-        err[str(n)] = {"phi_relmax": float((a - b).abs().max() / b.abs().max()),
-                       "pi_relmax": float((pa - pb).abs().max() / pb.abs().max()),
+        # FP64 error norms on the device (lf2_field_compare) against the FP64 run's buffers
+        cphi = lf2.lf2_field_compare(pairs["f32k"].fphi, pairs["f64"].front().data_ptr(), lf2.LF2_F64, 0, stream)
+        cpi = lf2.lf2_field_compare(pairs["f32k"].fpi, pairs["f64"].pi_front().data_ptr(), lf2.LF2_F64, 0, stream)
+        err[str(n)] = {"phi_relmax": cphi["relmax"], "phi_rel_l2": cphi["rel_l2"],
+                       "pi_relmax": cpi["relmax"], "pi_rel_l2": cpi["rel_l2"],
                        "energy_rel": abs(e32["total"] - e64["total"]) / abs(e64["total"])}
-        del a, pa
     for pair in pairs.values():
         pair.close()
     del pairs

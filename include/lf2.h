@@ -241,6 +241,19 @@ lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, d
 lf2_status lf2_leapfrog_energy(lf2_field phi, lf2_field pi, const lf2_params *p, int nsteps, double *dev_records,
                                void *stream);
 
+/* Error norms of a field against a reference array: the stated error of an FP32 run against
+ * the FP64 run of the same state (the paper has no counterpart).  Compares buffer `which` of
+ * f (as lf2_field_buffer: 0 = current value, 2 = current compensation) element by element
+ * with `ref`: sites*ncomp values of precision ref_prec (LF2_F64 for doubles, LF2_F32 or
+ * LF2_F32_KAHAN for floats) in the same layout, device memory, caller-owned.  Writes
+ *   out[0] = max |f - ref|,  out[1] = max |ref|,  out[2] = sum (f - ref)^2,  out[3] = sum ref^2
+ * (4 doubles, host), computed in FP64 on the device in a fixed order (bitwise reproducible);
+ * a NaN in either operand makes out[0] NaN.  Uses f's energy scratch (order calls on one
+ * stream, as for lf2_energy) and synchronises `stream`.  LF2_ERR_INVALID for NULL arguments,
+ * `which` outside 0..3 or an unknown ref_prec; LF2_ERR_STATE if that buffer does not exist. */
+lf2_status lf2_field_compare(lf2_field f, int which, const void *ref, lf2_precision ref_prec, double *out,
+                             void *stream);
+
 /* lf2_energy for callers that cannot allocate device memory.  The paper has no counterpart;
  * this entry point exists for callers whose device allocator belongs to someone else (a memory
  * pool or host framework that forbids cudaMalloc while it runs) or that must make no

@@ -536,6 +536,29 @@ lf2_status lf2_leapfrog_energy(lf2_field phi, lf2_field pi, const lf2_params *p,
     return LF2_OK;
 }
 
+lf2_status lf2_field_compare(lf2_field f, int which, const void *ref, lf2_precision ref_prec, double *out,
+                             void *stream) {
+    if (!f || !ref || !out) return fail(LF2_ERR_INVALID, "NULL argument");
+    if (ref_prec != LF2_F64 && ref_prec != LF2_F32_KAHAN && ref_prec != LF2_F32)
+        return fail(LF2_ERR_INVALID, "unknown reference precision %d", (int)ref_prec);
+    void *buf = nullptr;
+    lf2_status st = lf2_field_buffer(f, which, &buf);
+    if (st != LF2_OK) return st;
+    if (!buf) return fail(LF2_ERR_STATE, "buffer %d of this field does not exist", which);
+    st = ensure_energy_scratch(f);
+    if (st != LF2_OK) return st;
+    // values are in the storage type; compensation buffers (2, 3) are float
+    const bool a_double = which < 2 && f->prec == LF2_F64;
+    cudaStream_t s = (cudaStream_t)stream;
+    LF2_CUDA(launch_compare(buf, a_double, ref, ref_prec == LF2_F64, f->count, f->energy_scratch, s), "compare launch");
+    LF2_CUDA(cudaMemcpyAsync(f->energy_host, f->energy_scratch + kEnergyRecordOffset, 4 * sizeof(double),
+                             cudaMemcpyDeviceToHost, s),
+             "compare copy");
+    LF2_CUDA(cudaStreamSynchronize(s), "compare sync");
+    memcpy(out, f->energy_host, 4 * sizeof(double));
+    return LF2_OK;
+}
+
 lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream) {
     lf2_status st = check_pair(phi, pi);
     if (st == LF2_OK) st = check_params(p);

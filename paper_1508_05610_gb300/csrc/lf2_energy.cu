@@ -291,7 +291,84 @@ void step_energy_nc(const StepArgs &a, const CoefE &ke, int nb, double *scratch,
                                                                    (float *)a.pi, a.comp, a.g, k, ke, scratch, record);
 }
 
+// ------------------------------------------------------------ error norms (a12)
+// max |a - ref|, max |ref|, sum (a - ref)^2, sum ref^2 over n elements, FP64.  The maxima
+// propagate NaN (a NaN difference must not vanish from an error report).
+__device__ __forceinline__ double nanmax(double m, double x) { return (x > m || x != x) ? x : m; }
+
+constexpr int kCmp = 4;
+
+__device__ __forceinline__ void block_cmp(const double (&acc)[kCmp], double (&sh)[kCmp][kEnergyThreads]) {
+#pragma unroll
+    for (int j = 0; j < kCmp; ++j) sh[j][threadIdx.x] = acc[j];
+    __syncthreads();
+#pragma unroll
+    for (int w = kEnergyThreads / 2; w > 0; w >>= 1) {
+        for (int t = threadIdx.x; t < kCmp * w; t += kEnergyThreads) {
+            const int j = t / w, i = t % w;
+            sh[j][i] = j < 2 ? nanmax(sh[j][i], sh[j][i + w]) : __dadd_rn(sh[j][i], sh[j][i + w]);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename RA, typename RB>
+__global__ void __launch_bounds__(kEnergyThreads) k_compare(const RA *__restrict__ a, const RB *__restrict__ ref,
+                                                            long long n, double *__restrict__ scratch) {
+    __shared__ double sh[kCmp][kEnergyThreads];
+    __shared__ bool s_last;
+    double acc[kCmp] = {0.0, 0.0, 0.0, 0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double r = (double)__ldg(ref + i);
+        const double d = __dsub_rn((double)__ldg(a + i), r);
+        acc[0] = nanmax(acc[0], fabs(d));
+        acc[1] = nanmax(acc[1], fabs(r));
+        acc[2] = __fma_rn(d, d, acc[2]);
+        acc[3] = __fma_rn(r, r, acc[3]);
+    }
+    block_cmp(acc, sh);
+    if (threadIdx.x < kCmp) scratch[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+    __threadfence();
+    __syncthreads();
+    unsigned int *counter = reinterpret_cast<unsigned int *>(scratch + kEnergyCounterOffset);
+    if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double tot[kCmp] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < kCmp; ++j) {
+            const double v = __ldcg(scratch + (size_t)b * kEnergySlots + j);
+            tot[j] = j < 2 ? nanmax(tot[j], v) : __dadd_rn(tot[j], v);
+        }
+    }
+    block_cmp(tot, sh);
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < kCmp; ++j) scratch[kEnergyRecordOffset + j] = sh[j][0];
+        *counter = 0u;
+    }
+}
+
+template <typename RA>
+cudaError_t compare_ref(const RA *a, const void *ref, bool ref_double, long long n, int nb, double *scratch,
+                        cudaStream_t s) {
+    if (ref_double)
+        k_compare<RA, double><<<nb, kEnergyThreads, 0, s>>>(a, (const double *)ref, n, scratch);
+    else
+        k_compare<RA, float><<<nb, kEnergyThreads, 0, s>>>(a, (const float *)ref, n, scratch);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool ref_double, long long n,
+                           double *scratch, cudaStream_t s) {
+    const int nb = energy_grid(n);
+    if (a_double) return compare_ref<double>((const double *)a, ref, ref_double, n, nb, scratch, s);
+    return compare_ref<float>((const float *)a, ref, ref_double, n, nb, scratch, s);
+}
 
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
                           const lf2_params &p, double *scratch, double *record, cudaStream_t s) {

@@ -348,6 +348,10 @@ cudaError_t launch_tblock(const TbArgs &a, const TbConfig &c, cudaStream_t s);
 
 // Writes an lf2_energy_t-shaped record (16 doubles) from a result row to device memory.
 static_assert(sizeof(lf2_energy_t) == kEnergySlots * sizeof(double), "energy record layout");
+// Error norms of n elements a against ref (FP64): max |a - ref|, max |ref|, sum (a - ref)^2,
+// sum ref^2, written to scratch + kEnergyRecordOffset (energy scratch layout).  One launch.
+cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool ref_double, long long n,
+                           double *scratch, cudaStream_t s);
 
 // Fixed-size scratch of lf2_energy_noalloc (kEnergyScratchDoubles doubles, 78 KB).
 cudaError_t energy_noalloc_scratch(double **out);

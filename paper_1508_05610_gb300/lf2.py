@@ -80,6 +80,7 @@ SIGNATURES = {
     "lf2_energy_device": [_vp, _vp, ctypes.POINTER(lf2_params), _vp, _vp],
     "lf2_energy_noalloc": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
     "lf2_leapfrog_energy": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, _vp, _vp],
+    "lf2_field_compare": [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp],
     "lf2_ensemble_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(lf2_params),
                             ctypes.POINTER(_vp)],
     "lf2_ensemble_run": [_vp, ctypes.c_int, _vp],
@@ -237,6 +238,17 @@ def lf2_leapfrog_energy(phi, pi, p: lf2_params, nsteps, dev_records_ptr, stream=
     """nsteps leapfrog steps, one kernel each, that also write the energy record of the state at
     the start of every step (nsteps x 16 doubles of device memory at dev_records_ptr)."""
     _call("lf2_leapfrog_energy", phi, pi, ctypes.byref(p), int(nsteps), dev_records_ptr, _stream_ptr(stream))
+
+
+def lf2_field_compare(f, ref_ptr, ref_prec, which=0, stream=None) -> dict:
+    """Error norms of buffer `which` of f against a device array (FP64 on the device):
+    max_abs_diff, max_abs_ref, sum_sq_diff, sum_sq_ref, and the derived relmax / rel_l2."""
+    out = (ctypes.c_double * 4)()
+    _call("lf2_field_compare", f, int(which), ref_ptr, int(ref_prec), out, _stream_ptr(stream))
+    d = {"max_abs_diff": out[0], "max_abs_ref": out[1], "sum_sq_diff": out[2], "sum_sq_ref": out[3]}
+    d["relmax"] = out[0] / out[1] if out[1] > 0 else float("nan")
+    d["rel_l2"] = (out[2] / out[3]) ** 0.5 if out[3] > 0 else float("nan")
+    return d
 
 
 ENERGY_RECORD_FIELDS = ["kinetic", "gradient", "potential", "total"] + [f"sum{a}" for a in range(6)] + \
