@@ -112,6 +112,19 @@ def test_field_argument_checks_before_any_device_call(lib):
         with pytest.raises(lib.LF2Error) as e:
             lib.lf2_leapfrog(g, h, p, -1)
         assert e.value.status == lib.LF2_ERR_INVALID
+        # the fused step + energy and the error norms check their arguments first too
+        for args in ((f, g, p, 1, 0x5000), (g, g, p, 1, 0x5000), (g, h, bad, 1, 0x5000), (g, h, p, -1, 0x5000),
+                     (g, h, p, 2, None)):
+            with pytest.raises(lib.LF2Error) as e:
+                lib.lf2_leapfrog_energy(*args)
+            assert e.value.status == lib.LF2_ERR_INVALID, args
+        for which, ref, prec in ((0, None, lib.LF2_F64), (5, 0x5000, lib.LF2_F64), (0, 0x5000, 9)):
+            with pytest.raises(lib.LF2Error) as e:
+                lib.lf2_field_compare(g, ref, prec, which=which)
+            assert e.value.status == lib.LF2_ERR_INVALID, (which, ref, prec)
+        with pytest.raises(lib.LF2Error) as e:  # g was wrapped without a back buffer
+            lib.lf2_field_compare(g, 0x5000, lib.LF2_F64, which=1)
+        assert e.value.status == lib.LF2_ERR_STATE
         for x in (f, g, h):
             lib.lf2_field_free(x)
     finally:
