@@ -141,7 +141,8 @@ lf2_status lf2_field_alloc(lf2_lattice lat, int ncomp, lf2_precision prec, lf2_f
 lf2_status lf2_field_wrap(lf2_lattice lat, int ncomp, lf2_precision prec, void *const *dev_ptrs,
                           int nptrs, lf2_field *out);
 
-/* Frees the field and every buffer the library allocated for it. */
+/* Frees the field and every buffer the library allocated for it.  LF2_ERR_STATE (nothing
+ * freed) while the field is a member of an ensemble. */
 lf2_status lf2_field_free(lf2_field f);
 
 /* Device address of one of the field's buffers: which = 0 the current value buffer, 1 the
@@ -275,8 +276,8 @@ lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, 
  * lattice sizes, per-member parameters -- into a batched ensemble.  The paper runs many
  * independent fields only as separate programs; here they share every kernel launch.
  * Allocates the members' back buffers (temporal blocking needs them) and device tables.
- * The fields must stay alive and must not be used by another ensemble until
- * lf2_ensemble_destroy; their lattices cannot be destroyed meanwhile (LF2_ERR_STATE). */
+ * Until lf2_ensemble_destroy the fields cannot be freed or put into another ensemble, and
+ * their lattices cannot be destroyed (each returns LF2_ERR_STATE). */
 lf2_status lf2_ensemble_create(int n, const lf2_field *phis, const lf2_field *pis, const lf2_params *per_lattice,
                                lf2_ensemble *out);
 

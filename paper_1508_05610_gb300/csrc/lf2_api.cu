@@ -297,6 +297,7 @@ lf2_status lf2_field_wrap(lf2_lattice lat, int ncomp, lf2_precision prec, void *
 
 lf2_status lf2_field_free(lf2_field f) {
     if (!f) return fail(LF2_ERR_INVALID, "field is NULL");
+    if (f->ensemble) return fail(LF2_ERR_STATE, "field is a member of an ensemble: destroy the ensemble first");
     for (int i = 0; i < 2; ++i)
         if (f->own_val[i] && f->val[i]) cudaFree(f->val[i]);
     for (int i = 0; i < 2; ++i)

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -199,7 +200,12 @@ lf2_status lf2_ensemble_create(int n, const lf2_field *phis, const lf2_field *pi
             return set_error(LF2_ERR_INVALID, "member %d: phi and pi do not form a pair", m);
         if (a->prec != phis[0]->prec || a->ncomp != phis[0]->ncomp)
             return set_error(LF2_ERR_INVALID, "member %d: all members need one precision and component count", m);
-        if (!(per_lattice[m].dx > 0.0)) return set_error(LF2_ERR_INVALID, "member %d: dx must be > 0", m);
+        const lf2_params &q = per_lattice[m];
+        if (!(q.dx > 0.0) || !std::isfinite(q.dx) || !std::isfinite(q.dt) || !std::isfinite(q.lambda) ||
+            !std::isfinite(q.eta) || !std::isfinite(q.m2))
+            return set_error(LF2_ERR_INVALID, "member %d: dx must be finite and > 0, the other parameters finite", m);
+        if (a->ensemble || b->ensemble)
+            return set_error(LF2_ERR_STATE, "member %d: a field already belongs to another ensemble", m);
         for (int k = 0; k < m; ++k)
             if (phis[k] == a || pis[k] == b || phis[k] == b || pis[k] == a)
                 return set_error(LF2_ERR_INVALID, "member %d shares a field with member %d", m, k);
@@ -238,7 +244,10 @@ lf2_status lf2_ensemble_create(int n, const lf2_field *phis, const lf2_field *pi
         delete e;
         return st;
     }
-    for (int m = 0; m < n; ++m) e->phi[m]->lat->users++;
+    for (int m = 0; m < n; ++m) {
+        e->phi[m]->lat->users++;
+        e->phi[m]->ensemble = e->pi[m]->ensemble = e;
+    }
     *out = e;
     return LF2_OK;
 }
@@ -249,7 +258,10 @@ lf2_status lf2_ensemble_destroy(lf2_ensemble e) {
     if (e->d_items) cudaFree(e->d_items);
     if (e->d_counter) cudaFree(e->d_counter);
     if (e->capture) cudaStreamDestroy(e->capture);
-    for (int m = 0; m < e->n; ++m) e->phi[m]->lat->users--;
+    for (int m = 0; m < e->n; ++m) {
+        e->phi[m]->lat->users--;
+        e->phi[m]->ensemble = e->pi[m]->ensemble = nullptr;
+    }
     delete e;
     return LF2_OK;
 }

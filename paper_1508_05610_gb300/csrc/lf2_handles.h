@@ -29,6 +29,7 @@ struct lf2_field_s {
     int cfront = 0;
     double *energy_scratch = nullptr;  // kEnergyScratchDoubles: partial rows, record, counter (device)
     double *energy_host = nullptr;     // one pinned lf2_energy_t
+    lf2_ensemble ensemble = nullptr;   // the ensemble this field is a member of, if any
 };
 
 namespace lf2 {

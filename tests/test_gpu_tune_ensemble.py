@@ -140,6 +140,41 @@ def test_ensemble_tune_and_configs_bitwise(lf2):
             s.close()
 
 
+def test_ensemble_membership_is_enforced(lf2):
+    """A member field cannot be freed or join a second ensemble until the ensemble is gone."""
+    p = lf2.params(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    a, b = lf2.System((16, 8, 8), 1, "f32k"), lf2.System((24, 8, 8), 1, "f32k")
+    try:
+        e = lf2.lf2_ensemble_create([a.phi, b.phi], [a.pi, b.pi], [p, p])
+        try:
+            for f in (a.phi, b.pi):
+                with pytest.raises(lf2.LF2Error) as err:
+                    lf2.lf2_field_free(f)
+                assert err.value.status == lf2.LF2_ERR_STATE
+            with pytest.raises(lf2.LF2Error) as err:
+                lf2.lf2_ensemble_create([a.phi], [a.pi], [p])
+            assert err.value.status == lf2.LF2_ERR_STATE
+            with pytest.raises(lf2.LF2Error) as err:
+                lf2.lf2_lattice_destroy(a.lat)
+            assert err.value.status == lf2.LF2_ERR_STATE
+            bad = lf2.params(dx=1.0, dt=float("nan"), lam=1.0, eta=1.0, m2=0.0)
+            c = lf2.System((16, 8, 8), 1, "f32k")
+            try:
+                with pytest.raises(lf2.LF2Error) as err:
+                    lf2.lf2_ensemble_create([c.phi], [c.pi], [bad])
+                assert err.value.status == lf2.LF2_ERR_INVALID
+            finally:
+                c.close()
+            lf2.lf2_ensemble_run(e, 3)  # the ensemble still works
+        finally:
+            lf2.lf2_ensemble_destroy(e)
+        e2 = lf2.lf2_ensemble_create([a.phi], [a.pi], [p])  # free again after destroy
+        lf2.lf2_ensemble_destroy(e2)
+    finally:
+        a.close()
+        b.close()
+
+
 @pytest.mark.parametrize("prec,ncomp", [("f64", 2), ("f32k", 1), ("f32", 2)])
 def test_snapshot_format_and_exact_restart(lf2, tmp_path, prec, ncomp):
     """Snapshots are the paper's header-less row-major per-site component lists in the storage
