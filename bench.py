@@ -393,6 +393,30 @@ def cpu_baseline():
                       f"(OpenMP over z-planes), {dt:.1f} s"}
 
 
+def oracle_table():
+    """The CPU oracle on the workloads of the baseline plan, on this host's cores (one JSON
+    line): the 32^3 real lattice (dt 0.1, 100 steps) on one thread and on all threads, the
+    256^3 complex lattice for 10 steps and the 1024^3 real lattice for 2 steps on all threads.
+    The threaded runs are bitwise equal to single-thread ones (OpenMP over z-planes)."""
+    from oracle import oracle
+    from paper_1508_05610_gb300 import inputs
+    threads = os.cpu_count() or 1
+    rows = []
+    for n, c, dt, steps, th in ((32, 1, 0.1, 100, 1), (32, 1, 0.1, 100, threads), (256, 2, 0.05, 10, threads),
+                                (1024, 1, 0.05, 2, threads)):
+        kw = dict(dx=1.0, dt=dt, lam=1.0, eta=1.0, m2=0.0)
+        phi0 = inputs.gaussian_field(n, n, n, c, sigma=0.1, seed=inputs.BASE_SEED)
+        phi, pi = oracle.evolve(phi0, phi0 * 0.0, 0, half_kick=True, threads=th, **kw)
+        del phi0
+        t0 = time.perf_counter()
+        oracle.evolve(phi, pi, steps, threads=th, **kw)
+        sec = time.perf_counter() - t0
+        del phi, pi
+        rows.append({"lattice": [n, n, n], "ncomp": c, "steps": steps, "threads": th, "seconds": round(sec, 3),
+                     "gsu_per_s": round(n ** 3 * steps / sec / 1e9, 5)})
+    print(json.dumps({"oracle_table": rows, "cores": threads, "unit": UNIT}))
+
+
 def run_reference(args):
     rank = rank_info()[0]
     if rank != 0:  # the CPU reference runs once, on rank 0
@@ -429,7 +453,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lf2", choices=["lf2", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="time the CPU oracle on the baseline plan's workloads (host only) and exit")
     args = ap.parse_args()
+    if args.oracle_table:
+        oracle_table()
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
