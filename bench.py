@@ -335,6 +335,17 @@ def run_gpu(args):
                "peak_source": f"{peak_src} HBM copy bandwidth",
                "bytes_per_site_update": BYTES_PER_SITE[prec], "steps_per_launch": depth,
                "effective_frac": round(BYTES_PER_SITE[prec] * sites / per_step / 1e9 / hbm_peak, 4)}
+        if hbm["traffic"] is not None:
+            # ncu DRAM bytes of one launch per site-update it performs
+            hbm["dram_bytes_per_site_update"] = round(hbm["traffic"] / (sites * depth), 2)
+        if depth > 1:
+            # sites each stage computes per output site in the x-y plane: the tile plus its halo
+            # (depth rows, depth columns rounded up to whole thread groups), over whole tiles
+            c = cfgs[prec]
+            tp = -(-depth // c["cx"]) * c["cx"]
+            ntx, nty = -(-N // c["tile_x"]), -(-N // c["tile_y"])
+            hbm["halo_redundancy_xy"] = round(
+                ntx * nty * (c["tile_x"] + 2 * tp) * (c["tile_y"] + 2 * depth) / (N * N), 3)
         if prec != "f64":
             return hbm
         ginst = DP_INSTR_PER_SITE[NCOMP] * sites / per_step / 1e9
