@@ -352,7 +352,7 @@ def run_gpu(args):
         return {"bound": "alu", "achieved": round(ginst, 1), "peak": round(FP64_PEAK_GINST, 1),
                 "unit": "G FP64 instr/s", "frac": round(ginst / FP64_PEAK_GINST, 4),
                 "traffic": hbm["traffic"], "peak_source": "nominal FP64 rate 1.25 TFLOP/s = 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
-                "dp_instr_per_site_update": DP_INSTR_PER_SITE[NCOMP], "hbm": {k: hbm[k] for k in ("achieved", "peak", "frac")}}
+                "dp_instr_per_site_update": DP_INSTR_PER_SITE[NCOMP], "hbm": {k: hbm[k] for k in ("achieved", "peak", "frac", "dram_bytes_per_site_update") if k in hbm}}
 
     t64, t32 = results["f64"], results["f32k"]
     line = {
