@@ -27,9 +27,12 @@ def main(argv=None):
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=8)
-    ap.add_argument("--op", default="leapfrog", choices=["leapfrog", "derivative", "energy", "step_energy"],
+    ap.add_argument("--op", default="leapfrog",
+                    choices=["leapfrog", "derivative", "energy", "step_energy", "ensemble"],
                     help="derivative: time lf2_field_derivative along --dim; energy: time lf2_energy_device; "
-                         "step_energy: time lf2_leapfrog_energy (a step with its energy record per launch)")
+                         "step_energy: time lf2_leapfrog_energy (a step with its energy record per launch); "
+                         "ensemble: the 64-lattice FP32+Kahan ensemble (sides 64..192, lambda in [0.5, 2]), "
+                         "--steps per graph launch, --kernel tune or tblock with --depth/--cx/--tile")
     ap.add_argument("--dim", type=int, default=0)
     args = ap.parse_args(argv)
 
@@ -38,6 +41,9 @@ def main(argv=None):
     from . import build, inputs, lf2
     build.build()
     lf2.load()
+    if args.op == "ensemble":
+        run_ensemble(args, torch, lf2, inputs)
+        return
     nx, ny, nz = (args.n * 3)[:3] if len(args.n) == 1 else args.n
     stream = torch.cuda.current_stream()
     p = lf2.params(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
@@ -123,6 +129,51 @@ def main(argv=None):
     sites = nx * ny * nz
     print(json.dumps({"lattice": [nx, ny, nz], "ncomp": args.ncomp, "prec": args.prec, "config": cfg,
                       "steps": args.steps, "seconds": t, "gsu_per_s": sites * args.steps / t / 1e9}))
+
+
+def run_ensemble(args, torch, lf2, inputs):
+    """The batched ensemble: 64 real lattices with sides drawn from {64, 96, 128, 160, 192} and
+    lambda uniform in [0.5, 2] (seeded), FP32 + Kahan, dt = 0.05, one graph launch per run."""
+    stream = torch.cuda.current_stream()
+    members = inputs.ensemble_members()
+    keep, fields, plist, sites = [], [], [], 0
+    for side, lam, seed in members:
+        phi = inputs.gaussian_field_device(side, side, side, 1, sigma=0.1, seed=seed, dtype=torch.float32)
+        pi = torch.zeros_like(phi)
+        lat = lf2.lf2_lattice_create((side, side, side))
+        fields.append((lat, lf2.lf2_field_wrap(lat, 1, lf2.LF2_F32_KAHAN, [phi.data_ptr()]),
+                       lf2.lf2_field_wrap(lat, 1, lf2.LF2_F32_KAHAN, [pi.data_ptr()])))
+        keep += [phi, pi]
+        sites += side ** 3
+        plist.append(lf2.params(dx=1.0, dt=0.05, lam=lam, eta=1.0))
+        lf2.lf2_leapfrog_init(fields[-1][1], fields[-1][2], plist[-1], stream)
+    e = lf2.lf2_ensemble_create([f[1] for f in fields], [f[2] for f in fields], plist)
+    try:
+        if args.kernel in ("tune", "auto"):
+            cfg = lf2.lf2_ensemble_tune(e, stream=stream)
+        else:
+            tx, ty = (int(v) for v in args.tile.split("x"))
+            cfg = {"kernel": KERNELS[args.kernel], "depth": args.depth, "cx": args.cx, "tile_x": tx, "tile_y": ty}
+            lf2.lf2_ensemble_set_config(e, **cfg)
+        lf2.lf2_ensemble_run(e, args.steps, stream)  # capture + warm-up
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):  # best of three timed runs
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lf2.lf2_ensemble_run(e, args.steps, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            best = t if best is None else min(best, t)
+    finally:
+        lf2.lf2_ensemble_destroy(e)
+        for lat, fphi, fpi in fields:
+            lf2.lf2_field_free(fphi)
+            lf2.lf2_field_free(fpi)
+            lf2.lf2_lattice_destroy(lat)
+    print(json.dumps({"op": "ensemble", "members": len(members), "sites": sites, "config": cfg,
+                      "steps": args.steps, "seconds": best, "gsu_per_s": sites * args.steps / best / 1e9}))
 
 
 if __name__ == "__main__":
