@@ -34,6 +34,9 @@ def main(argv=None):
                          "ensemble: the 64-lattice FP32+Kahan ensemble (sides 64..192, lambda in [0.5, 2]), "
                          "--steps per graph launch, --kernel tune or tblock with --depth/--cx/--tile")
     ap.add_argument("--dim", type=int, default=0)
+    ap.add_argument("--serial", action="store_true",
+                    help="with --op ensemble: run the members one after another with lf2_leapfrog and "
+                         "their own tuned plans instead of as one ensemble")
     args = ap.parse_args(argv)
 
     import torch
@@ -147,6 +150,27 @@ def run_ensemble(args, torch, lf2, inputs):
         sites += side ** 3
         plist.append(lf2.params(dx=1.0, dt=0.05, lam=lam, eta=1.0))
         lf2.lf2_leapfrog_init(fields[-1][1], fields[-1][2], plist[-1], stream)
+    if args.serial:
+        try:
+            for (lat, fphi, fpi), p in zip(fields, plist):
+                lf2.lf2_tune(fphi, fpi, p, stream=stream)
+                lf2.lf2_leapfrog(fphi, fpi, p, 4, stream)  # warm-up with the plan
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for (lat, fphi, fpi), p in zip(fields, plist):
+                lf2.lf2_leapfrog(fphi, fpi, p, args.steps, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+        finally:
+            for lat, fphi, fpi in fields:
+                lf2.lf2_field_free(fphi)
+                lf2.lf2_field_free(fpi)
+                lf2.lf2_lattice_destroy(lat)
+        print(json.dumps({"op": "ensemble", "serial": True, "members": len(members), "sites": sites,
+                          "steps": args.steps, "seconds": t, "gsu_per_s": sites * args.steps / t / 1e9}))
+        return
     e = lf2.lf2_ensemble_create([f[1] for f in fields], [f[2] for f in fields], plist)
     try:
         if args.kernel in ("tune", "auto"):
