@@ -565,6 +565,10 @@ lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, 
     if (st == LF2_OK) st = check_params(p);
     if (st != LF2_OK) return st;
     if (!out) return fail(LF2_ERR_INVALID, "output pointer is NULL");
+    const long long needed = energy_scratch_needed(phi->lat->sites);
+    if (needed > kEnergyScratchDoubles)
+        return fail(LF2_ERR_UNSUPPORTED, "energy reduction needs %lld scratch doubles, the fixed array holds %d",
+                    needed, kEnergyScratchDoubles);
     double *scratch = nullptr;
     LF2_CUDA(energy_noalloc_scratch(&scratch), "cudaGetSymbolAddress(energy scratch)");
     cudaStream_t s = (cudaStream_t)stream;

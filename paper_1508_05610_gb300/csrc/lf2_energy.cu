@@ -370,6 +370,10 @@ cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool r
     return compare_ref<float>((const float *)a, ref, ref_double, n, nb, scratch, s);
 }
 
+long long energy_scratch_needed(long long sites) {
+    return (long long)energy_grid(sites) * kEnergySlots + kEnergySlots + 1;
+}
+
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
                           const lf2_params &p, double *scratch, double *record, cudaStream_t s) {
     const CoefE k = make_coefE(p);

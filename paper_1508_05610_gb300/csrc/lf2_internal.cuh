@@ -102,8 +102,10 @@ static_assert(sizeof(lf2_energy_t) == kEnergySlots * sizeof(double), "energy rec
 cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool ref_double, long long n,
                            double *scratch, cudaStream_t s);
 
-// Fixed-size scratch of lf2_energy_noalloc (kEnergyScratchDoubles doubles, 78 KB).
+// Fixed-size scratch of lf2_energy_noalloc (kEnergyScratchDoubles doubles, 78 KB), and the
+// doubles one reduction over `sites` sites uses (partial rows, record, counter).
 cudaError_t energy_noalloc_scratch(double **out);
+long long energy_scratch_needed(long long sites);
 
 // Conversions between host-side doubles and storage precision.
 cudaError_t launch_convert_from_f64(const double *src, void *dst, long long n, lf2_precision prec, cudaStream_t s);
