@@ -249,6 +249,61 @@ __device__ __forceinline__ void update_f32_site2(f32x2 c, f32x2 xm, f32x2 xp, f3
     }
 }
 
+// update_f32 for one site of NC >= 3 components: |phi|^2 and the potential coefficient in
+// scalar exactly as force_f32 forms them, the components in packed pairs (0,1), (2,3), ...
+// with update_f32_site2's per-component sequence, and an odd last component in scalar with
+// update_f32's own sequence (-g c = RN(ng * c) since ng = -g exactly).
+template <int NC, bool KAHAN>
+__device__ __forceinline__ void update_f32_siteN(const float (&c)[NC], const float (&xm)[NC], const float (&xp)[NC],
+                                                 const float (&ym)[NC], const float (&yp)[NC], const float (&zm)[NC],
+                                                 const float (&zp)[NC], float (&p)[NC], float (&cmp)[NC],
+                                                 float (&out)[NC], const Coef32x2 &k, const Coef32 &ks) {
+    float s2 = __fmul_rn(c[0], c[0]);
+#pragma unroll
+    for (int b = 1; b < NC; ++b) s2 = __fmaf_rn(c[b], c[b], s2);
+    const float ngs = __fmaf_rn(-ks.lam, __fsub_rn(s2, ks.eta2), -ks.m2);  // -g
+    const f32x2 ng = pk2(ngs, ngs);
+#pragma unroll
+    for (int q = 0; q < NC / 2; ++q) {
+        const int a0 = 2 * q, a1 = 2 * q + 1;
+        const f32x2 C = pk2(c[a0], c[a1]);
+        const f32x2 dx_ = add2(sub2(pk2(xm[a0], xm[a1]), C), sub2(pk2(xp[a0], xp[a1]), C));
+        const f32x2 dy_ = add2(sub2(pk2(ym[a0], ym[a1]), C), sub2(pk2(yp[a0], yp[a1]), C));
+        const f32x2 dz_ = add2(sub2(pk2(zm[a0], zm[a1]), C), sub2(pk2(zp[a0], zp[a1]), C));
+        const f32x2 d = add2(add2(dx_, dy_), dz_);
+        const f32x2 F = fma2(d, k.inv_dx2, mul2(ng, C));
+        f32x2 P = fma2(k.dt, F, pk2(p[a0], p[a1]));
+        f32x2 O;
+        if (KAHAN) {
+            const f32x2 ny = fma2(k.ndt, P, pk2(cmp[a0], cmp[a1]));
+            const f32x2 t = sub2(C, ny);
+            up2(add2(sub2(t, C), ny), cmp[a0], cmp[a1]);
+            O = t;
+        } else {
+            O = fma2(k.dt, P, C);
+        }
+        up2(P, p[a0], p[a1]);
+        up2(O, out[a0], out[a1]);
+    }
+    if constexpr (NC % 2 == 1) {
+        constexpr int a = NC - 1;
+        const float dx_ = __fadd_rn(__fsub_rn(xm[a], c[a]), __fsub_rn(xp[a], c[a]));
+        const float dy_ = __fadd_rn(__fsub_rn(ym[a], c[a]), __fsub_rn(yp[a], c[a]));
+        const float dz_ = __fadd_rn(__fsub_rn(zm[a], c[a]), __fsub_rn(zp[a], c[a]));
+        const float d = __fadd_rn(__fadd_rn(dx_, dy_), dz_);
+        const float F = __fmaf_rn(d, ks.inv_dx2, __fmul_rn(ngs, c[a]));
+        p[a] = __fmaf_rn(ks.dt, F, p[a]);
+        if (KAHAN) {
+            const float y = __fmaf_rn(ks.dt, p[a], -cmp[a]);
+            const float t = __fadd_rn(c[a], y);
+            cmp[a] = __fsub_rn(__fsub_rn(t, c[a]), y);
+            out[a] = t;
+        } else {
+            out[a] = __fmaf_rn(ks.dt, p[a], c[a]);
+        }
+    }
+}
+
 // ----------------------------------------------------------------- geometry helpers
 struct Geom {
     int nx, ny, nz;

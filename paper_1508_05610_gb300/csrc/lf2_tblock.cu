@@ -16,14 +16,22 @@ constexpr int kTbMaxThreads = 512;  // the kernels' launch bound
 }  // namespace
 
 bool tblock_supported(const TbArgs &a, TbConfig &c) {
-    if (a.ncomp > 2) return false;
-    if (c.depth == 0) c.depth = 4;
-    if (c.depth != 2 && c.depth != 3 && c.depth != 4 && c.depth != 6 && c.depth != 8) return false;
     const int esz = a.prec == LF2_F64 ? 8 : 4;
-    if (c.cx == 0) c.cx = (esz == 8 && a.ncomp == 2) ? 1 : 2;
-    if (c.cx != 1 && c.cx != 2 && c.cx != 4) return false;
-    if (c.cx * a.ncomp * esz > 16) return false;  // one vector of at most 16 bytes per thread and plane
-    if (c.cx == 4 && (esz != 4 || a.ncomp != 1)) return false;
+    if (a.ncomp > 2) {
+        // 3, 4 or 6 components, FP32 storage: one column per thread, depth 2 to 4 (2 for 6
+        // components); FP64 stays on the one-step kernels, which its FP64 arithmetic bounds
+        if (esz == 8 || (a.ncomp != 3 && a.ncomp != 4 && a.ncomp != 6)) return false;
+        if (c.depth == 0) c.depth = a.ncomp == 6 ? 2 : 3;
+        if (c.cx == 0) c.cx = 1;
+        if (c.cx != 1 || c.depth < 2 || c.depth > (a.ncomp == 6 ? 2 : 4)) return false;
+    } else {
+        if (c.depth == 0) c.depth = 4;
+        if (c.depth != 2 && c.depth != 3 && c.depth != 4 && c.depth != 6 && c.depth != 8) return false;
+        if (c.cx == 0) c.cx = (esz == 8 && a.ncomp == 2) ? 1 : 2;
+        if (c.cx != 1 && c.cx != 2 && c.cx != 4) return false;
+        if (c.cx * a.ncomp * esz > 16) return false;  // one vector of at most 16 bytes per thread and plane
+        if (c.cx == 4 && (esz != 4 || a.ncomp != 1)) return false;
+    }
     if ((long long)a.g.nx * a.g.ny * a.ncomp >= (1LL << 31)) return false;
     if (c.tile_x == 0) c.tile_x = 32;
     if (c.tile_y == 0) c.tile_y = 16;
@@ -53,7 +61,9 @@ bool tblock_supported(const TbArgs &a, TbConfig &c) {
         }
     }
     if (c.zchunk < 1) return false;
-    const uintptr_t align = (uintptr_t)c.cx * a.ncomp * esz;
+    // the accesses are chunks of the largest of 16, 8, 4 bytes dividing a thread's bytes
+    const int bytes = c.cx * a.ncomp * esz;
+    const uintptr_t align = bytes % 16 == 0 ? 16 : (bytes % 8 == 0 ? 8 : 4);
     if (((uintptr_t)a.phi | (uintptr_t)a.phi_out | (uintptr_t)a.pi | (uintptr_t)a.pi_out | (uintptr_t)a.comp |
          (uintptr_t)a.comp_out) % align)
         return false;

@@ -45,38 +45,65 @@ struct VecOf<16> {
     using T = float4;
 };
 
-// N contiguous elements of R as one vector access (N * sizeof(R) in {4, 8, 16}).
+// N contiguous elements of R as vector accesses of CH bytes, CH the largest of 16, 8, 4 that
+// divides the N elements' size: one access for 4, 8 or 16 bytes (every 1- and 2-component
+// case), three for the 12 and 24 bytes of a 3- or 6-component site, whose address is only
+// 4- or 8-byte aligned.
+template <typename R, int N>
+struct VecChunk {
+    static constexpr int BYTES = N * (int)sizeof(R);
+    static constexpr int CH = BYTES % 16 == 0 ? 16 : (BYTES % 8 == 0 ? 8 : 4);
+    static constexpr int COUNT = BYTES / CH;
+    static constexpr int E = CH / (int)sizeof(R);
+    using V = typename VecOf<CH>::T;
+};
+
 template <typename R, int N>
 __device__ __forceinline__ void vload_g(const R *__restrict__ p, R (&v)[N]) {
-    using V = typename VecOf<N * sizeof(R)>::T;
-    V t = __ldg(reinterpret_cast<const V *>(p));
-    memcpy(v, &t, sizeof(V));
+    using C = VecChunk<R, N>;
+#pragma unroll
+    for (int q = 0; q < C::COUNT; ++q) {
+        typename C::V t = __ldg(reinterpret_cast<const typename C::V *>(p) + q);
+        memcpy(&v[q * C::E], &t, C::CH);
+    }
 }
 template <typename R, int N>
 __device__ __forceinline__ void vload_cg(const R *__restrict__ p, R (&v)[N]) {
-    using V = typename VecOf<N * sizeof(R)>::T;
-    V t = __ldcg(reinterpret_cast<const V *>(p));
-    memcpy(v, &t, sizeof(V));
+    using C = VecChunk<R, N>;
+#pragma unroll
+    for (int q = 0; q < C::COUNT; ++q) {
+        typename C::V t = __ldcg(reinterpret_cast<const typename C::V *>(p) + q);
+        memcpy(&v[q * C::E], &t, C::CH);
+    }
 }
 template <typename R, int N>
 __device__ __forceinline__ void vstore_g(R *__restrict__ p, const R (&v)[N]) {
-    using V = typename VecOf<N * sizeof(R)>::T;
-    V t;
-    memcpy(&t, v, sizeof(V));
-    *reinterpret_cast<V *>(p) = t;
+    using C = VecChunk<R, N>;
+#pragma unroll
+    for (int q = 0; q < C::COUNT; ++q) {
+        typename C::V t;
+        memcpy(&t, &v[q * C::E], C::CH);
+        reinterpret_cast<typename C::V *>(p)[q] = t;
+    }
 }
 template <typename R, int N>
 __device__ __forceinline__ void vload_s(const R *p, R (&v)[N]) {
-    using V = typename VecOf<N * sizeof(R)>::T;
-    V t = *reinterpret_cast<const V *>(p);
-    memcpy(v, &t, sizeof(V));
+    using C = VecChunk<R, N>;
+#pragma unroll
+    for (int q = 0; q < C::COUNT; ++q) {
+        typename C::V t = reinterpret_cast<const typename C::V *>(p)[q];
+        memcpy(&v[q * C::E], &t, C::CH);
+    }
 }
 template <typename R, int N>
 __device__ __forceinline__ void vstore_s(R *p, const R (&v)[N]) {
-    using V = typename VecOf<N * sizeof(R)>::T;
-    V t;
-    memcpy(&t, v, sizeof(V));
-    *reinterpret_cast<V *>(p) = t;
+    using C = VecChunk<R, N>;
+#pragma unroll
+    for (int q = 0; q < C::COUNT; ++q) {
+        typename C::V t;
+        memcpy(&t, &v[q * C::E], C::CH);
+        reinterpret_cast<typename C::V *>(p)[q] = t;
+    }
 }
 
 __device__ __forceinline__ int wrap_any(int v, int n) {
@@ -204,6 +231,34 @@ __device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__re
                     up2(o[a], out[e0], out[e1]);
                     up2(p[a], st.pq[s][e0], st.pq[s][e1]);
                     if (MODE == 1) up2(cm[a], st.cq[s][e0], st.cq[s][e1]);
+                }
+            }
+        } else if constexpr (MODE != 3 && NC >= 3) {
+            // FP32 with 3 to 6 components: the components of a site in packed pairs
+            const Coef32x2 k2 = make_coef32x2(k, k.zero);
+#pragma unroll
+            for (int j = 0; j < CX; ++j) {
+                float c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], o[NC];
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e = j * NC + a;
+                    c[a] = st.lv[s - 1][1][e];
+                    xm[a] = (j == 0) ? left[a] : st.lv[s - 1][1][e - NC];
+                    xp[a] = (j == CX - 1) ? right[a] : st.lv[s - 1][1][e + NC];
+                    ym[a] = dn[e];
+                    yp[a] = up[e];
+                    zm[a] = st.lv[s - 1][0][e];
+                    zp[a] = st.lv[s - 1][2][e];
+                    p[a] = st.pq[s][e];
+                    cm[a] = (MODE == 1) ? st.cq[s][e] : 0.0f;
+                }
+                update_f32_siteN<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, o, k2, k);
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const int e = j * NC + a;
+                    out[e] = o[a];
+                    st.pq[s][e] = p[a];
+                    if (MODE == 1) st.cq[s][e] = cm[a];
                 }
             }
         } else {
@@ -417,16 +472,32 @@ cudaError_t launch_ens_t(const TbEnsembleLaunch &e, cudaStream_t s) {
 // each precision's instantiations live in their own translation unit.
 template <typename R, int NC, int MODE, typename CoefT>
 cudaError_t launch_prec(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStream_t s) {
-    switch (c.cx * 16 + c.depth) {
+    if constexpr (NC >= 3) {
+        // 3 to 6 components: one column per thread; the per-column state grows with NC, so
+        // 6 components run at depth 2 only (within the 128 registers of a 512-thread block)
+        if (c.cx != 1) return cudaErrorNotSupported;
+        switch (c.depth) {
+            case 2: return launch_t<R, NC, MODE, 2, 1, CoefT>(a, c, k, s);
+            case 3:
+                if constexpr (NC <= 4) return launch_t<R, NC, MODE, 3, 1, CoefT>(a, c, k, s);
+                return cudaErrorNotSupported;
+            case 4:
+                if constexpr (NC <= 4) return launch_t<R, NC, MODE, 4, 1, CoefT>(a, c, k, s);
+                return cudaErrorNotSupported;
+            default: return cudaErrorNotSupported;
+        }
+    } else {
+        switch (c.cx * 16 + c.depth) {
 #define LF2_TB_CASE(CXV, TV)                                                                      \
-    case CXV * 16 + TV:                                                                           \
-        if constexpr (CXV * NC * sizeof(R) <= 16) return launch_t<R, NC, MODE, TV, CXV, CoefT>(a, c, k, s); \
-        return cudaErrorNotSupported;
-        LF2_TB_CASE(1, 2) LF2_TB_CASE(1, 3) LF2_TB_CASE(1, 4) LF2_TB_CASE(1, 6) LF2_TB_CASE(1, 8)
-        LF2_TB_CASE(2, 2) LF2_TB_CASE(2, 3) LF2_TB_CASE(2, 4) LF2_TB_CASE(2, 6) LF2_TB_CASE(2, 8)
-        LF2_TB_CASE(4, 2) LF2_TB_CASE(4, 3) LF2_TB_CASE(4, 4) LF2_TB_CASE(4, 6) LF2_TB_CASE(4, 8)
+        case CXV * 16 + TV:                                                                           \
+            if constexpr (CXV * NC * sizeof(R) <= 16) return launch_t<R, NC, MODE, TV, CXV, CoefT>(a, c, k, s); \
+            return cudaErrorNotSupported;
+            LF2_TB_CASE(1, 2) LF2_TB_CASE(1, 3) LF2_TB_CASE(1, 4) LF2_TB_CASE(1, 6) LF2_TB_CASE(1, 8)
+            LF2_TB_CASE(2, 2) LF2_TB_CASE(2, 3) LF2_TB_CASE(2, 4) LF2_TB_CASE(2, 6) LF2_TB_CASE(2, 8)
+            LF2_TB_CASE(4, 2) LF2_TB_CASE(4, 3) LF2_TB_CASE(4, 4) LF2_TB_CASE(4, 6) LF2_TB_CASE(4, 8)
 #undef LF2_TB_CASE
-        default: return cudaErrorNotSupported;
+            default: return cudaErrorNotSupported;
+        }
     }
 }
 

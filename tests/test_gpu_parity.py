@@ -254,6 +254,64 @@ def test_n_component_fields_fp32_and_integer_bitwise(lf2, ora, prec):
     assert np.array_equal(phi, ophi) and np.array_equal(pi, opi)
 
 
+@pytest.mark.parametrize("prec", ["f32k", "f32"])
+@pytest.mark.parametrize("shape,ncomp", [((40, 16, 9), 3), ((24, 12, 7), 4), ((33, 10, 6), 6), ((20, 6, 5), 3)])
+def test_n_component_tblock_bitwise_identical_to_single_steps(lf2, prec, shape, ncomp):
+    """Temporal blocking of 3, 4 and 6 components (packed component pairs, 12- and 24-byte
+    sites in chunked accesses): every depth it runs, ragged tiles and z-chunks, odd x extents,
+    bit for bit the one-thread-per-site kernel."""
+    nx, ny, nz = shape
+    kw = TB_PARAMS[0]
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.5, seed=19)
+    pi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=20)
+    steps = 9
+    ref = run_gpu(lf2, phi0, pi0, steps, prec, kw, kernel=lf2.LF2_KERNEL_SITE)
+    ran = 0
+    for depth in (2, 3, 4, 6):
+        for tile_x, tile_y in ((8, 4), (16, 8), (24, 8), (12, 6), (28, 12)):
+            # built: depth 2-4 (2 for 6 components), at most 512 threads (tile plus halo)
+            built = depth in ((2,) if ncomp == 6 else (2, 3, 4)) and \
+                (tile_x + 2 * depth) * (tile_y + 2 * depth) <= 512
+            for zchunk in (0, 4):
+                cfg = (depth, tile_x, tile_y, zchunk)
+                try:
+                    got = run_gpu(lf2, phi0, pi0, steps, prec, kw, kernel=lf2.LF2_KERNEL_TBLOCK, depth=depth, cx=1,
+                                  tile_x=tile_x, tile_y=tile_y, zchunk=zchunk)
+                except lf2.LF2Error as e:
+                    assert e.status == lf2.LF2_ERR_UNSUPPORTED and not built, (e, cfg)
+                    continue
+                assert built, cfg
+                ran += 1
+                assert np.array_equal(got[0], ref[0]), cfg
+                assert np.array_equal(got[1], ref[1]), cfg
+                assert got[2]["total"] == ref[2]["total"], cfg
+    assert ran == (10 if ncomp == 6 else 26)
+    # two columns per thread are not built for 3+ components
+    with pytest.raises(lf2.LF2Error) as e:
+        run_gpu(lf2, phi0, pi0, steps, prec, kw, kernel=lf2.LF2_KERNEL_TBLOCK, depth=2, cx=2, tile_x=16, tile_y=8)
+    assert e.value.status == lf2.LF2_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("ncomp", [3, 4, 6])
+def test_n_component_tblock_parity_with_oracle_and_integer_exact(lf2, ora, ncomp):
+    nx, ny, nz = 36, 14, 11
+    kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.3, seed=211)
+    pi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=212)
+    ophi, opi = ora.evolve(phi0, pi0, 10, half_kick=True, **kw)
+    depth = 2 if ncomp == 6 else 4
+    phi, pi, _ = run_gpu(lf2, phi0, pi0, 10, "f32k", kw, kernel=lf2.LF2_KERNEL_TBLOCK, depth=depth, cx=1,
+                         tile_x=24, tile_y=8)
+    assert relmax(phi, ophi) <= 1e-5 and relmax(pi, opi) <= 1e-5
+    ikw = dict(dx=1.0, dt=1.0, lam=0.0, eta=0.0, m2=0.0)
+    i0 = inputs.integer_field(nx, ny, nz, ncomp, lo=-4, hi=4, seed=213)
+    j0 = inputs.integer_field(nx, ny, nz, ncomp, lo=-4, hi=4, seed=214)
+    ophi, opi = ora.evolve(i0, j0, 4, **ikw)
+    phi, pi, _ = run_gpu(lf2, i0, j0, 4, "f32", ikw, half_kick=False, kernel=lf2.LF2_KERNEL_TBLOCK, depth=2, cx=1,
+                         tile_x=16, tile_y=8)
+    assert np.array_equal(phi, ophi) and np.array_equal(pi, opi)
+
+
 # ------------------------------------------------ the paper's field operation: derivative
 @pytest.mark.parametrize("prec,ncomp", [("f64", 1), ("f64", 3), ("f32", 2), ("f32k", 6)])
 @pytest.mark.parametrize("dim", [0, 1, 2])
