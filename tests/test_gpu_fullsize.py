@@ -166,6 +166,24 @@ def test_1536cube_complex_fp32_kahan_tuned_sampled(env, ora):
     torch.cuda.empty_cache()
 
 
+def test_256cube_complex_fp32_kahan_tuned_sampled(env, ora):
+    """The benchmark's FP32 + Kahan leg: 256^3 complex, the tuner's plan (temporal blocking),
+    sampled sites within 1e-5 of the FP64 oracle after 10 steps."""
+    torch, lf2 = env
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    phi = inputs.gaussian_field_device(256, 256, 256, 2, sigma=0.1, seed=inputs.BASE_SEED, dtype=torch.float32)
+    sites = sample_sites(256, 8, seed=5)
+    boxes = [box_of(torch, phi, c, HALF) for c in sites]
+    out_phi, out_pi = evolve_wrapped_tuned(torch, lf2, phi, lf2.LF2_F32_KAHAN, lf2.params(**kw), STEPS)
+    for center, box in zip(sites, boxes):
+        bphi, bpi = ora.evolve(box, np.zeros_like(box), STEPS, half_kick=True, **kw)
+        x, y, z = center
+        got_phi = out_phi[z, y, x].double().cpu().numpy()
+        got_pi = out_pi[z, y, x].double().cpu().numpy()
+        assert np.max(np.abs(got_phi - bphi[HALF, HALF, HALF])) <= 1e-5 * np.max(np.abs(bphi)), center
+        assert np.max(np.abs(got_pi - bpi[HALF, HALF, HALF])) <= 1e-5 * np.max(np.abs(bpi)), center
+
+
 def test_ensemble_of_64_lattices_members_match_standalone(env):
     """The 64-lattice ensemble (sides from {64, 96, 128, 160, 192}, lambda ~ U[0.5, 2], FP32 with
     the compensated drift, per-lattice seeds): after one tuned ensemble run, every member is
