@@ -34,7 +34,7 @@ def run_site(lf2, shape, ncomp, prec, phi0, pi0, kw, steps):
         return s.download()
 
 
-@pytest.mark.parametrize("prec,ncomp", [("f32k", 1), ("f32", 2), ("f64", 1)])
+@pytest.mark.parametrize("prec,ncomp", [("f32k", 1), ("f32", 2), ("f64", 1), ("f32k", 3), ("f32", 4), ("f32k", 6)])
 def test_tune_leaves_fields_untouched_and_plan_is_bitwise(lf2, prec, ncomp):
     shape = (64, 48, 40)
     kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
