@@ -56,7 +56,7 @@ typedef enum {
     LF2_ERR_UNSUPPORTED = 2, /* valid in the paper's model but not built: dim != 3, ncomp > 2 */
     LF2_ERR_NOMEM = 3,       /* a device or host allocation failed */
     LF2_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
-    LF2_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (ensemble runs) */
+    LF2_ERR_TIMEOUT = 5,     /* reserved for a bounded device-side wait that gave up; no call returns it */
     LF2_ERR_STATE = 6        /* call not allowed in the object's current state */
 } lf2_status;
 
@@ -230,11 +230,15 @@ lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, d
  * k = 0 .. nsteps-1, the energy record of the state at the start of step k (phi_k and the
  * synchronised pi_k, as lf2_energy defines them) to dev_records + 16 k: nsteps lf2_energy_t
  * records in device memory, caller-owned.  The paper's programs report diagnostics every step;
- * here each step is ONE kernel that reads the stencil once for both the energy and the update
- * (kick and drift), visiting the sites in the order and with the arithmetic of lf2_energy, so
- * each record is bitwise the one lf2_energy_device gives for that state.  Meant for runs with
- * an energy every step: the kernel is the one-thread-per-site one, not the tiled kernels of
- * lf2_leapfrog.  Enqueues on `stream` without waiting; after the first call on phi (which may
+ * here each step reads the stencil once for both the energy and the update (kick and drift),
+ * visiting the sites in the order and with the arithmetic of lf2_energy, so each record is
+ * bitwise the one lf2_energy_device gives for that state.  Meant for runs with an energy every
+ * step: the kernel is the one-thread-per-site one, not the tiled kernels of lf2_leapfrog.
+ * A lattice of at most 303 x 256 sites runs all nsteps (>= 2) in one cooperative launch with a
+ * grid barrier between steps; larger ones run one launch per step.  Results are the same bits
+ * either way.  A barrier that does not complete within about a second (all blocks of a
+ * cooperative launch are resident, so it always completes) ends the run and leaves NaN in the
+ * records from that step on.  Enqueues on `stream` without waiting; after the first call on phi (which may
  * allocate its back buffer and energy scratch, so make it outside a stream capture) calls
  * allocate nothing and can be captured into a CUDA graph.  Calls on one phi share its energy
  * scratch with lf2_energy and lf2_energy_device: order them on one stream.

@@ -528,6 +528,14 @@ lf2_status lf2_leapfrog_energy(lf2_field phi, lf2_field pi, const lf2_params *p,
     st = ensure_dynamic(phi, s);
     if (st == LF2_OK) st = ensure_energy_scratch(phi);
     if (st != LF2_OK) return st;
+    // small lattices: all steps in one cooperative launch (bitwise the per-step launches)
+    const cudaError_t e = launch_steps_energy(step_args(phi, pi, p, p->dt, true), nsteps, phi->energy_scratch,
+                                              dev_records, s);
+    if (e == cudaSuccess) {
+        if (nsteps & 1) phi->front = 1 - phi->front;
+        return LF2_OK;
+    }
+    if (e != cudaErrorNotSupported) return cuda_fail(e, "multi-step step+energy launch");
     for (int k = 0; k < nsteps; ++k) {
         const StepArgs a = step_args(phi, pi, p, p->dt, true);
         LF2_CUDA(launch_step_energy(a, phi->energy_scratch, dev_records + (size_t)k * kEnergySlots, s),

@@ -32,10 +32,20 @@ template <int NC>
 constexpr int kNs = 3 + 2 * NC;
 constexpr int kKin = 0, kGrad = 1, kPot = 2, kSum = 3;
 
-template <typename R, int NC>
+// L2 loads (COHERENT) where other blocks of the same launch wrote the data; the read-only
+// path otherwise.  The values are the same either way.
+template <bool COHERENT, typename R>
+__device__ __forceinline__ R ld_field(const R *p) {
+    if constexpr (COHERENT)
+        return __ldcg(p);
+    else
+        return __ldg(p);
+}
+
+template <typename R, int NC, bool COHERENT = false>
 __device__ __forceinline__ void load_d(const R *__restrict__ f, long long s, double (&v)[NC]) {
 #pragma unroll
-    for (int a = 0; a < NC; ++a) v[a] = (double)__ldg(f + s * NC + a);
+    for (int a = 0; a < NC; ++a) v[a] = (double)ld_field<COHERENT>(f + s * NC + a);
 }
 
 // Adds one site's raw sums to acc.  c: phi_n at the site, xm..zp: its neighbours in the order
@@ -82,6 +92,39 @@ __device__ __forceinline__ void block_sum(const double (&acc)[NS], double (&sh)[
     }
 }
 
+// Sums `nrows` partial rows (L2 reads, in row order) with the block and writes the record
+// (thread 0) to `record` and, when not NULL, to `own`.  All threads of the block take part.
+template <int NC>
+__device__ __forceinline__ void reduce_rows(const double *rows, int nrows, double (&sh)[kNs<NC>][kEnergyThreads],
+                                            const CoefE &k, double *__restrict__ record, double *__restrict__ own) {
+    constexpr int NS = kNs<NC>;
+    double tot[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) tot[j] = 0.0;
+    for (int b = threadIdx.x; b < nrows; b += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) tot[j] = __dadd_rn(tot[j], __ldcg(rows + (size_t)b * kEnergySlots + j));
+    }
+    block_sum<NS>(tot, sh);
+    if (threadIdx.x == 0) {
+        double r[kEnergySlots];
+        double ssq = 0.0;
+        for (int a = 0; a < NC; ++a) ssq += sh[kSum + NC + a][0];
+        r[0] = k.vol * (0.5 * sh[kKin][0]);
+        r[1] = k.vol * (0.5 * k.inv_dx2 * sh[kGrad][0]);
+        r[2] = k.vol * (0.25 * k.lam * sh[kPot][0] + 0.5 * k.m2 * ssq);
+        r[3] = r[0] + r[1] + r[2];
+        for (int a = 0; a < kMaxComp; ++a) {
+            r[4 + a] = a < NC ? sh[kSum + a][0] : 0.0;
+            r[4 + kMaxComp + a] = a < NC ? sh[kSum + NC + a][0] : 0.0;
+        }
+        for (int j = 0; j < kEnergySlots; ++j) {
+            if (own) own[j] = r[j];
+            if (record) record[j] = r[j];
+        }
+    }
+}
+
 // End of every energy kernel: stores this block's partial row, and the last block to get here
 // sums all rows (in block order) and writes the record.  No block waits for another.
 template <int NC>
@@ -99,33 +142,8 @@ __device__ __forceinline__ void finish_energy(const double (&acc)[kNs<NC>], doub
     __syncthreads();
     if (!s_last) return;
     __threadfence();  // every other block's row is visible to this one
-    double tot[NS];
-#pragma unroll
-    for (int j = 0; j < NS; ++j) tot[j] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-#pragma unroll
-        for (int j = 0; j < NS; ++j) tot[j] = __dadd_rn(tot[j], __ldcg(scratch + (size_t)b * kEnergySlots + j));
-    }
-    block_sum<NS>(tot, sh);
-    if (threadIdx.x == 0) {
-        double r[kEnergySlots];
-        double ssq = 0.0;
-        for (int a = 0; a < NC; ++a) ssq += sh[kSum + NC + a][0];
-        r[0] = k.vol * (0.5 * sh[kKin][0]);
-        r[1] = k.vol * (0.5 * k.inv_dx2 * sh[kGrad][0]);
-        r[2] = k.vol * (0.25 * k.lam * sh[kPot][0] + 0.5 * k.m2 * ssq);
-        r[3] = r[0] + r[1] + r[2];
-        for (int a = 0; a < kMaxComp; ++a) {
-            r[4 + a] = a < NC ? sh[kSum + a][0] : 0.0;
-            r[4 + kMaxComp + a] = a < NC ? sh[kSum + NC + a][0] : 0.0;
-        }
-        double *own = scratch + kEnergyRecordOffset;
-        for (int j = 0; j < kEnergySlots; ++j) {
-            own[j] = r[j];
-            if (record) record[j] = r[j];
-        }
-        *counter = 0u;  // ready for the next launch on this scratch
-    }
+    reduce_rows<NC>(scratch, (int)gridDim.x, sh, k, record, scratch + kEnergyRecordOffset);
+    if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch on this scratch
 }
 
 // Linear indices of the six periodic neighbours of site s.
@@ -167,8 +185,76 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(const R *__restrict__
     finish_energy<NC>(acc, sh, scratch, k, record);
 }
 
-// Fused step + energy, FP64: the energy of (phi_n, pi_{n-1/2}) and the step to
-// (phi_{n+1}, pi_{n+1/2}) from one read of each site's stencil.
+// One site of a fused step + energy, FP64: adds the energy of (phi_n, pi_{n-1/2}) at site s
+// to acc and writes the step to (phi_{n+1}, pi_{n+1/2}), from one read of the site's stencil.
+template <int NC, bool COHERENT>
+__device__ __forceinline__ void site_step_energy_f64(const double *__restrict__ phi, double *__restrict__ phi_out,
+                                                     double *__restrict__ pi, long long s, const Geom &g,
+                                                     const Coef64 &k, const CoefE &ke, double (&acc)[kNs<NC>]) {
+    const Nbr n = neighbours(s, g);
+    double c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], out[NC];
+    load_d<double, NC, COHERENT>(phi, s, c);
+    load_d<double, NC, COHERENT>(phi, n.xm, xm);
+    load_d<double, NC, COHERENT>(phi, n.xp, xp);
+    load_d<double, NC, COHERENT>(phi, n.ym, ym);
+    load_d<double, NC, COHERENT>(phi, n.yp, yp);
+    load_d<double, NC, COHERENT>(phi, n.zm, zm);
+    load_d<double, NC, COHERENT>(phi, n.zp, zp);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) p[a] = pi[s * NC + a];
+    energy_site<NC>(c, xm, xp, ym, yp, zm, zp, p, acc, ke);
+    update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, out, k);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        pi[s * NC + a] = p[a];
+        phi_out[s * NC + a] = out[a];
+    }
+}
+
+// The same for FP32 storage (KAHAN: compensated drift); the energy is computed in FP64 from
+// the exact conversions of the stored values.
+template <int NC, bool KAHAN, bool COHERENT>
+__device__ __forceinline__ void site_step_energy_f32(const float *__restrict__ phi, float *__restrict__ phi_out,
+                                                     float *__restrict__ pi, float *__restrict__ comp, long long s,
+                                                     const Geom &g, const Coef32 &k, const CoefE &ke,
+                                                     double (&acc)[kNs<NC>]) {
+    const Nbr n = neighbours(s, g);
+    float c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], out[NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        c[a] = ld_field<COHERENT>(phi + s * NC + a);
+        xm[a] = ld_field<COHERENT>(phi + n.xm * NC + a);
+        xp[a] = ld_field<COHERENT>(phi + n.xp * NC + a);
+        ym[a] = ld_field<COHERENT>(phi + n.ym * NC + a);
+        yp[a] = ld_field<COHERENT>(phi + n.yp * NC + a);
+        zm[a] = ld_field<COHERENT>(phi + n.zm * NC + a);
+        zp[a] = ld_field<COHERENT>(phi + n.zp * NC + a);
+        p[a] = pi[s * NC + a];
+        cm[a] = KAHAN ? comp[s * NC + a] : 0.0f;
+    }
+    double dc[NC], dxm[NC], dxp[NC], dym[NC], dyp[NC], dzm[NC], dzp[NC], dp[NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        dc[a] = c[a];
+        dxm[a] = xm[a];
+        dxp[a] = xp[a];
+        dym[a] = ym[a];
+        dyp[a] = yp[a];
+        dzm[a] = zm[a];
+        dzp[a] = zp[a];
+        dp[a] = p[a];
+    }
+    energy_site<NC>(dc, dxm, dxp, dym, dyp, dzm, dzp, dp, acc, ke);
+    update_f32<NC, KAHAN>(c, xm, xp, ym, yp, zm, zp, p, cm, out, k);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        pi[s * NC + a] = p[a];
+        phi_out[s * NC + a] = out[a];
+        if (KAHAN) comp[s * NC + a] = cm[a];
+    }
+}
+
+// Fused step + energy, one step per launch.
 template <int NC>
 __global__ void __launch_bounds__(kEnergyThreads)
     k_step_energy_f64(const double *__restrict__ phi, double *__restrict__ phi_out, double *__restrict__ pi, Geom g,
@@ -178,31 +264,11 @@ __global__ void __launch_bounds__(kEnergyThreads)
 #pragma unroll
     for (int j = 0; j < kNs<NC>; ++j) acc[j] = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride) {
-        const Nbr n = neighbours(s, g);
-        double c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], out[NC];
-        load_d<double, NC>(phi, s, c);
-        load_d<double, NC>(phi, n.xm, xm);
-        load_d<double, NC>(phi, n.xp, xp);
-        load_d<double, NC>(phi, n.ym, ym);
-        load_d<double, NC>(phi, n.yp, yp);
-        load_d<double, NC>(phi, n.zm, zm);
-        load_d<double, NC>(phi, n.zp, zp);
-#pragma unroll
-        for (int a = 0; a < NC; ++a) p[a] = pi[s * NC + a];
-        energy_site<NC>(c, xm, xp, ym, yp, zm, zp, p, acc, ke);
-        update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, out, k);
-#pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            pi[s * NC + a] = p[a];
-            phi_out[s * NC + a] = out[a];
-        }
-    }
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
+        site_step_energy_f64<NC, false>(phi, phi_out, pi, s, g, k, ke, acc);
     finish_energy<NC>(acc, sh, scratch, ke, record);
 }
 
-// Fused step + energy, FP32 storage (KAHAN: compensated drift); the energy is computed in FP64
-// from the exact conversions of the stored values.
 template <int NC, bool KAHAN>
 __global__ void __launch_bounds__(kEnergyThreads)
     k_step_energy_f32(const float *__restrict__ phi, float *__restrict__ phi_out, float *__restrict__ pi,
@@ -213,43 +279,118 @@ __global__ void __launch_bounds__(kEnergyThreads)
 #pragma unroll
     for (int j = 0; j < kNs<NC>; ++j) acc[j] = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride) {
-        const Nbr n = neighbours(s, g);
-        float c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], out[NC];
-#pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            c[a] = __ldg(phi + s * NC + a);
-            xm[a] = __ldg(phi + n.xm * NC + a);
-            xp[a] = __ldg(phi + n.xp * NC + a);
-            ym[a] = __ldg(phi + n.ym * NC + a);
-            yp[a] = __ldg(phi + n.yp * NC + a);
-            zm[a] = __ldg(phi + n.zm * NC + a);
-            zp[a] = __ldg(phi + n.zp * NC + a);
-            p[a] = pi[s * NC + a];
-            cm[a] = KAHAN ? comp[s * NC + a] : 0.0f;
-        }
-        double dc[NC], dxm[NC], dxp[NC], dym[NC], dyp[NC], dzm[NC], dzp[NC], dp[NC];
-#pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            dc[a] = c[a];
-            dxm[a] = xm[a];
-            dxp[a] = xp[a];
-            dym[a] = ym[a];
-            dyp[a] = yp[a];
-            dzm[a] = zm[a];
-            dzp[a] = zp[a];
-            dp[a] = p[a];
-        }
-        energy_site<NC>(dc, dxm, dxp, dym, dyp, dzm, dzp, dp, acc, ke);
-        update_f32<NC, KAHAN>(c, xm, xp, ym, yp, zm, zp, p, cm, out, k);
-#pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            pi[s * NC + a] = p[a];
-            phi_out[s * NC + a] = out[a];
-            if (KAHAN) comp[s * NC + a] = cm[a];
-        }
-    }
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
+        site_step_energy_f32<NC, KAHAN, false>(phi, phi_out, pi, comp, s, g, k, ke, acc);
     finish_energy<NC>(acc, sh, scratch, ke, record);
+}
+
+// ------------------------------------------- many fused steps in one launch (small lattices)
+// On a small lattice (the 32^3 run with an energy every step) a step costs a few microseconds
+// of arithmetic and about as much again in launch gaps and in the serial reduction.  One
+// cooperative launch runs all steps: the same grid, site order and per-site code as
+// k_step_energy, a grid barrier between steps, and block 0 reducing step k's partial rows
+// while the other blocks run step k+1 (the rows alternate between two sets).  The fields and
+// every record are bitwise those of one launch per step.
+
+// Barrier slots (arrivals, generation, error) in the scratch's last partial row, which the
+// two row sets (at most kStepsMaxBlocks rows each) leave free.
+constexpr int kStepsMaxBlocks = (kEnergyBlocks - 1) / 2;
+constexpr size_t kBarrierOffset = (size_t)(kEnergyBlocks - 1) * kEnergySlots;
+// A barrier waits at most about a second (2^24 polls of >= 64 ns); co-residency, which the
+// cooperative launch guarantees, keeps real waits to microseconds.
+constexpr unsigned kBarrierPolls = 1u << 24;
+
+// Grid barrier with a bounded wait: false if the wait ran out here or in another block.
+__device__ __forceinline__ bool grid_sync(unsigned *bar) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();  // this block's writes are visible device-wide before it arrives
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned polls = 0;
+            while (*gen == g) {
+                if (++polls > kBarrierPolls) {
+                    atomicExch(bar + 2, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile unsigned *)(bar + 2) != 0u) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// A run cut short by a barrier that did not complete leaves NaN records from that step on.
+__device__ __forceinline__ void poison_records(double *records, int from, int nsteps) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int j = from; j < nsteps; ++j)
+        for (int i = 0; i < kEnergySlots; ++i) records[(size_t)j * kEnergySlots + i] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kEnergyThreads)
+    k_steps_energy_f64(double *phi_a, double *phi_b, double *__restrict__ pi, Geom g, Coef64 k, CoefE ke, int nsteps,
+                       double *__restrict__ scratch, double *__restrict__ records) {
+    constexpr int NS = kNs<NC>;
+    __shared__ double sh[NS][kEnergyThreads];
+    unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int step = 0; step < nsteps; ++step) {
+        const double *src = (step & 1) ? phi_b : phi_a;
+        double *dst = (step & 1) ? phi_a : phi_b;
+        double acc[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) acc[j] = 0.0;
+        for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
+            site_step_energy_f64<NC, true>(src, dst, pi, s, g, k, ke, acc);
+        double *rows = scratch + (size_t)(step & 1) * gridDim.x * kEnergySlots;
+        block_sum<NS>(acc, sh);
+        if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+        if (!grid_sync(bar)) {
+            poison_records(records, step, nsteps);
+            return;
+        }
+        if (blockIdx.x == 0) reduce_rows<NC>(rows, (int)gridDim.x, sh, ke, records + (size_t)step * kEnergySlots, nullptr);
+    }
+}
+
+template <int NC, bool KAHAN>
+__global__ void __launch_bounds__(kEnergyThreads)
+    k_steps_energy_f32(float *phi_a, float *phi_b, float *__restrict__ pi, float *__restrict__ comp, Geom g, Coef32 k,
+                       CoefE ke, int nsteps, double *__restrict__ scratch, double *__restrict__ records) {
+    constexpr int NS = kNs<NC>;
+    __shared__ double sh[NS][kEnergyThreads];
+    unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int step = 0; step < nsteps; ++step) {
+        const float *src = (step & 1) ? phi_b : phi_a;
+        float *dst = (step & 1) ? phi_a : phi_b;
+        double acc[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) acc[j] = 0.0;
+        for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
+            site_step_energy_f32<NC, KAHAN, true>(src, dst, pi, comp, s, g, k, ke, acc);
+        double *rows = scratch + (size_t)(step & 1) * gridDim.x * kEnergySlots;
+        block_sum<NS>(acc, sh);
+        if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+        if (!grid_sync(bar)) {
+            poison_records(records, step, nsteps);
+            return;
+        }
+        if (blockIdx.x == 0) reduce_rows<NC>(rows, (int)gridDim.x, sh, ke, records + (size_t)step * kEnergySlots, nullptr);
+    }
 }
 
 // One block per 256 sites up to kEnergyBlocks: small lattices (a 32^3 run with an energy every
@@ -361,7 +502,62 @@ cudaError_t compare_ref(const RA *a, const void *ref, bool ref_double, long long
     return cudaGetLastError();
 }
 
+// Cooperative launch of k (grid nb) when every block can be resident at once.
+template <typename K, typename... Args>
+cudaError_t launch_cooperative(K kern, int nb, cudaStream_t s, Args... args) {
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kEnergyThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (!coop || (long long)per_sm * sms < nb) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kEnergyThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <int NC>
+cudaError_t steps_energy_nc(const StepArgs &a, int nsteps, int nb, const CoefE &ke, double *scratch, double *records,
+                            cudaStream_t s) {
+    if (a.prec == LF2_F64)
+        return launch_cooperative(k_steps_energy_f64<NC>, nb, s, (double *)a.phi, (double *)a.phi_out, (double *)a.pi,
+                                  a.g, make_coef64(a.p, a.dt), ke, nsteps, scratch, records);
+    const Coef32 k = make_coef32(a.p, a.dt);
+    if (a.prec == LF2_F32_KAHAN)
+        return launch_cooperative(k_steps_energy_f32<NC, true>, nb, s, (float *)a.phi, (float *)a.phi_out,
+                                  (float *)a.pi, a.comp, a.g, k, ke, nsteps, scratch, records);
+    return launch_cooperative(k_steps_energy_f32<NC, false>, nb, s, (float *)a.phi, (float *)a.phi_out, (float *)a.pi,
+                              a.comp, a.g, k, ke, nsteps, scratch, records);
+}
+
 }  // namespace
+
+cudaError_t launch_steps_energy(const StepArgs &a, int nsteps, double *scratch, double *records, cudaStream_t s) {
+    const int nb = energy_grid(a.g.sites);
+    if (!a.drift || nsteps < 2 || nb > kStepsMaxBlocks) return cudaErrorNotSupported;
+    // the barrier's arrival count, generation and error flag start at zero
+    cudaError_t e = cudaMemsetAsync(scratch + kBarrierOffset, 0, 4 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const CoefE ke = make_coefE(a.p);
+    switch (a.ncomp) {
+        case 1: return steps_energy_nc<1>(a, nsteps, nb, ke, scratch, records, s);
+        case 2: return steps_energy_nc<2>(a, nsteps, nb, ke, scratch, records, s);
+        case 3: return steps_energy_nc<3>(a, nsteps, nb, ke, scratch, records, s);
+        case 4: return steps_energy_nc<4>(a, nsteps, nb, ke, scratch, records, s);
+        case 5: return steps_energy_nc<5>(a, nsteps, nb, ke, scratch, records, s);
+        case 6: return steps_energy_nc<6>(a, nsteps, nb, ke, scratch, records, s);
+        default: return cudaErrorNotSupported;
+    }
+}
 
 cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool ref_double, long long n,
                            double *scratch, cudaStream_t s) {

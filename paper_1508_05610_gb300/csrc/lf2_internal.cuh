@@ -46,6 +46,11 @@ cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int nc
 // the state it starts from to `record`, with the site order and reduction of launch_energy, so
 // the record is bitwise the one launch_energy gives for that state.  One launch.
 cudaError_t launch_step_energy(const StepArgs &a, double *scratch, double *record, cudaStream_t s);
+// nsteps such steps in one cooperative launch (grid barriers between steps), writing
+// records[0 .. nsteps) and leaving phi in a.phi_out if nsteps is odd, else in a.phi;
+// cudaErrorNotSupported (nothing launched) unless the lattice is small enough for every block
+// of the reduction grid to be resident at once and nsteps >= 2.  Bitwise the per-step launches.
+cudaError_t launch_steps_energy(const StepArgs &a, int nsteps, double *scratch, double *records, cudaStream_t s);
 
 // Temporal blocking: `depth` fused steps per pass over x-y tiles of tile_x x tile_y output
 // sites (plus a depth-site halo), z-chunks of `zchunk` planes.  Unlike the one-step kernels it
