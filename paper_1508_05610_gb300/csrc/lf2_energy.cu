@@ -288,9 +288,10 @@ __global__ void __launch_bounds__(kEnergyThreads)
 // On a small lattice (the 32^3 run with an energy every step) a step costs a few microseconds
 // of arithmetic and about as much again in launch gaps and in the serial reduction.  One
 // cooperative launch runs all steps: the same grid, site order and per-site code as
-// k_step_energy, a grid barrier between steps, and block 0 reducing step k's partial rows
-// while the other blocks run step k+1 (the rows alternate between two sets).  The fields and
-// every record are bitwise those of one launch per step.
+// k_step_energy for the site blocks, a grid barrier between steps, and one extra block, which
+// owns no sites, reducing step k's partial rows while the site blocks run step k+1 (the rows
+// alternate between two sets).  The fields and every record are bitwise those of one launch
+// per step.
 
 // Barrier slots (arrivals, generation, error) in the scratch's last partial row, which the
 // two row sets (at most kStepsMaxBlocks rows each) leave free.
@@ -334,7 +335,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar) {
 
 // A run cut short by a barrier that did not complete leaves NaN records from that step on.
 __device__ __forceinline__ void poison_records(double *records, int from, int nsteps) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (blockIdx.x != gridDim.x - 1 || threadIdx.x != 0) return;
     for (int j = from; j < nsteps; ++j)
         for (int i = 0; i < kEnergySlots; ++i) records[(size_t)j * kEnergySlots + i] = __longlong_as_double(0x7ff8000000000000LL);
 }
@@ -346,23 +347,26 @@ __global__ void __launch_bounds__(kEnergyThreads)
     constexpr int NS = kNs<NC>;
     __shared__ double sh[NS][kEnergyThreads];
     unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int nsb = (int)gridDim.x - 1;  // site blocks; the last block reduces
+    const long long stride = (long long)nsb * blockDim.x;
     for (int step = 0; step < nsteps; ++step) {
         const double *src = (step & 1) ? phi_b : phi_a;
         double *dst = (step & 1) ? phi_a : phi_b;
         double acc[NS];
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = 0.0;
-        for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
-            site_step_energy_f64<NC, true>(src, dst, pi, s, g, k, ke, acc);
-        double *rows = scratch + (size_t)(step & 1) * gridDim.x * kEnergySlots;
-        block_sum<NS>(acc, sh);
-        if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+        double *rows = scratch + (size_t)(step & 1) * nsb * kEnergySlots;
+        if ((int)blockIdx.x < nsb) {
+            for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
+                site_step_energy_f64<NC, true>(src, dst, pi, s, g, k, ke, acc);
+            block_sum<NS>(acc, sh);
+            if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+        }
         if (!grid_sync(bar)) {
             poison_records(records, step, nsteps);
             return;
         }
-        if (blockIdx.x == 0) reduce_rows<NC>(rows, (int)gridDim.x, sh, ke, records + (size_t)step * kEnergySlots, nullptr);
+        if ((int)blockIdx.x == nsb) reduce_rows<NC>(rows, nsb, sh, ke, records + (size_t)step * kEnergySlots, nullptr);
     }
 }
 
@@ -373,23 +377,26 @@ __global__ void __launch_bounds__(kEnergyThreads)
     constexpr int NS = kNs<NC>;
     __shared__ double sh[NS][kEnergyThreads];
     unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int nsb = (int)gridDim.x - 1;  // site blocks; the last block reduces
+    const long long stride = (long long)nsb * blockDim.x;
     for (int step = 0; step < nsteps; ++step) {
         const float *src = (step & 1) ? phi_b : phi_a;
         float *dst = (step & 1) ? phi_a : phi_b;
         double acc[NS];
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = 0.0;
-        for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
-            site_step_energy_f32<NC, KAHAN, true>(src, dst, pi, comp, s, g, k, ke, acc);
-        double *rows = scratch + (size_t)(step & 1) * gridDim.x * kEnergySlots;
-        block_sum<NS>(acc, sh);
-        if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+        double *rows = scratch + (size_t)(step & 1) * nsb * kEnergySlots;
+        if ((int)blockIdx.x < nsb) {
+            for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
+                site_step_energy_f32<NC, KAHAN, true>(src, dst, pi, comp, s, g, k, ke, acc);
+            block_sum<NS>(acc, sh);
+            if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+        }
         if (!grid_sync(bar)) {
             poison_records(records, step, nsteps);
             return;
         }
-        if (blockIdx.x == 0) reduce_rows<NC>(rows, (int)gridDim.x, sh, ke, records + (size_t)step * kEnergySlots, nullptr);
+        if ((int)blockIdx.x == nsb) reduce_rows<NC>(rows, nsb, sh, ke, records + (size_t)step * kEnergySlots, nullptr);
     }
 }
 
@@ -525,9 +532,11 @@ cudaError_t launch_cooperative(K kern, int nb, cudaStream_t s, Args... args) {
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// nb site blocks plus the reducing block
 template <int NC>
 cudaError_t steps_energy_nc(const StepArgs &a, int nsteps, int nb, const CoefE &ke, double *scratch, double *records,
                             cudaStream_t s) {
+    nb += 1;
     if (a.prec == LF2_F64)
         return launch_cooperative(k_steps_energy_f64<NC>, nb, s, (double *)a.phi, (double *)a.phi_out, (double *)a.pi,
                                   a.g, make_coef64(a.p, a.dt), ke, nsteps, scratch, records);
@@ -542,7 +551,7 @@ cudaError_t steps_energy_nc(const StepArgs &a, int nsteps, int nb, const CoefE &
 }  // namespace
 
 cudaError_t launch_steps_energy(const StepArgs &a, int nsteps, double *scratch, double *records, cudaStream_t s) {
-    const int nb = energy_grid(a.g.sites);
+    const int nb = energy_grid(a.g.sites);  // site blocks, as for one launch per step
     if (!a.drift || nsteps < 2 || nb > kStepsMaxBlocks) return cudaErrorNotSupported;
     // the barrier's arrival count, generation and error flag start at zero
     cudaError_t e = cudaMemsetAsync(scratch + kBarrierOffset, 0, 4 * sizeof(unsigned), s);
