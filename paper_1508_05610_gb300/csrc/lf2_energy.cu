@@ -529,7 +529,12 @@ cudaError_t launch_cooperative(K kern, int nb, cudaStream_t s, Args... args) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
+    const cudaError_t r = cudaLaunchKernelEx(&cfg, kern, args...);
+    if (r == cudaErrorCooperativeLaunchTooLarge || r == cudaErrorNotSupported) {
+        (void)cudaGetLastError();  // not launched: the caller runs one launch per step instead
+        return cudaErrorNotSupported;
+    }
+    return r;
 }
 
 // nb site blocks plus the reducing block
