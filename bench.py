@@ -433,7 +433,7 @@ def run_reference(args):
     if rank != 0:  # the CPU reference runs once, on rank 0
         return
     threads = os.cpu_count() or 1
-    nz_slab = 16
+    nz_slab = 64  # several z-planes per host thread
     from oracle import oracle
     from paper_1508_05610_gb300 import inputs
     phi0 = inputs.gaussian_field(N, N, nz_slab, NCOMP, sigma=0.1, seed=inputs.BASE_SEED)
