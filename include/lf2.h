@@ -182,7 +182,9 @@ lf2_status lf2_field_derivative(lf2_field src, lf2_field dst, int dim, double dx
 
 /* Binned power spectrum of component `comp` of a field on a cubic N^3 lattice (the paper's
  * FFT is for cubic lattices, Sec. 3.6): P(k) = |phi~(k)|^2 / N^3 with phi~(k) = sum_x phi(x)
- * exp(-i k.x), k_i = 2 pi m_i / (N dx).  Mode (m_x, m_y, m_z) (signed integer frequencies)
+ * exp(-i k.x), k_i = 2 pi m_i / (N dx); comp = -1 sums the components' powers,
+ * sum_a |phi~_a(k)|^2 / N^3 (for a complex field, in every shell the mean of |FFT(phi_0 + i phi_1)|^2
+ * / N^3, since the cross terms cancel between k and -k).  Mode (m_x, m_y, m_z) (signed integer frequencies)
  * belongs to shell b = floor(sqrt(m_x^2 + m_y^2 + m_z^2)); shells b < nbins (<= 1024) are
  * returned as host arrays of nbins doubles: mean power, mean |k|, mode count.  The transform is
  * cuFFT (single or double precision after the storage type); buffers and the plan are

@@ -136,17 +136,19 @@ def derivative(phi, dim, dx=1.0) -> np.ndarray:
 def power_spectrum(phi, comp=0, nbins=32, dx=1.0):
     """Binned power spectrum of one component of a field on a cubic N^3 lattice (the paper's FFT
     is for cubic lattices, Sec. 3.6): P(k) = |phi~(k)|^2 / V with phi~(k) = sum_x phi(x)
-    exp(-i k.x), k_i = 2 pi m_i / (N dx) for the signed integer frequency m_i.  Mode (m_x, m_y,
-    m_z) belongs to bin b = floor(sqrt(m_x^2 + m_y^2 + m_z^2)) (an exact integer square root).
-    Returns (mean power, mean |k|, mode count) per bin b < nbins.  numpy's FFT is the
-    transform; the binning is a plain loop over the modes of the full spectrum."""
-    a = _field(phi)[..., comp]
-    nz, ny, nx = a.shape
+    exp(-i k.x), k_i = 2 pi m_i / (N dx) for the signed integer frequency m_i.  comp = -1 sums
+    the components' powers, sum_a |phi~_a(k)|^2 / V.  Mode (m_x, m_y, m_z) belongs to bin
+    b = floor(sqrt(m_x^2 + m_y^2 + m_z^2)) (an exact integer square root).  Returns (mean power,
+    mean |k|, mode count) per bin b < nbins.  numpy's FFT is the transform; the binning is a
+    plain loop over the modes of the full spectrum."""
+    f = _field(phi)
+    comps = range(f.shape[-1]) if comp == -1 else [comp]
+    nz, ny, nx = f.shape[:3]
     if not nx == ny == nz:
         raise ValueError("the power spectrum is defined for cubic lattices")
     n = nx
     V = n ** 3
-    F = np.fft.fftn(a)
+    F2 = sum(np.abs(np.fft.fftn(f[..., a])) ** 2 for a in comps)
     m = [int(v) for v in np.fft.fftfreq(n) * n]
     power = np.zeros(nbins)
     ksum = np.zeros(nbins)
@@ -157,7 +159,7 @@ def power_spectrum(phi, comp=0, nbins=32, dx=1.0):
                 s2 = m[ix] ** 2 + m[iy] ** 2 + m[iz] ** 2
                 b = math.isqrt(s2)
                 if b < nbins:
-                    power[b] += abs(F[iz, iy, ix]) ** 2 / V
+                    power[b] += F2[iz, iy, ix] / V
                     ksum[b] += 2 * math.pi / (n * dx) * math.sqrt(s2)
                     count[b] += 1
     with np.errstate(invalid="ignore", divide="ignore"):

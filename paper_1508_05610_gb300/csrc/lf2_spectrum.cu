@@ -1,5 +1,5 @@
-// lf2_spectrum.cu -- binned power spectrum of one field component (a diagnostic; the
-// paper's PlanFFT role, Sec. 3.6, for cubic lattices as there).
+// lf2_spectrum.cu -- binned power spectrum of one field component, or of all components
+// summed (a diagnostic; the paper's PlanFFT role, Sec. 3.6, for cubic lattices as there).
 //
 // P(k) = |phi~(k)|^2 / V with phi~(k) = sum_x phi(x) exp(-i k.x), k_i = 2 pi m_i / (N dx).
 // Mode (m_x, m_y, m_z) goes to shell b = floor(sqrt(m_x^2 + m_y^2 + m_z^2)), an exact integer
@@ -37,9 +37,11 @@ __device__ __forceinline__ int isqrt_exact(long long s) {
     return (int)b;
 }
 
+// add_power: add this component's power to the rows a previous component's binning wrote,
+// leaving the |k| sums and mode counts (the same for every component) as they are.
 template <typename C>
 __global__ void __launch_bounds__(kBinThreads) k_bin(const C *__restrict__ spec, int n, int nbins, double kunit,
-                                                     double inv_volume, double *__restrict__ partials) {
+                                                     double inv_volume, double *__restrict__ partials, int add_power) {
     extern __shared__ double hist[];  // 3 * nbins: power, |k| sum, count
     for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) hist[i] = 0.0;
     __syncthreads();
@@ -61,7 +63,12 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(const C *__restrict__ spec,
         atomicAdd(&hist[2 * nbins + b], w);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) partials[(size_t)blockIdx.x * 3 * nbins + i] = hist[i];
+    double *row = partials + (size_t)blockIdx.x * 3 * nbins;
+    if (add_power) {
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x) row[i] += hist[i];
+    } else {
+        for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) row[i] = hist[i];
+    }
 }
 
 __global__ void k_bin_final(const double *__restrict__ partials, int nblocks, int nbins, double *__restrict__ out) {
@@ -80,7 +87,7 @@ extern "C" lf2_status lf2_power_spectrum(lf2_field f, int comp, int nbins, doubl
     const int *n3 = f->lat->n;
     if (n3[0] != n3[1] || n3[1] != n3[2])
         return set_error(LF2_ERR_UNSUPPORTED, "the power spectrum needs a cubic lattice (as the paper's FFT)");
-    if (comp < 0 || comp >= f->ncomp) return set_error(LF2_ERR_INVALID, "component %d out of range", comp);
+    if (comp < -1 || comp >= f->ncomp) return set_error(LF2_ERR_INVALID, "component %d out of range", comp);
     if (nbins < 1 || nbins > kMaxBins) return set_error(LF2_ERR_INVALID, "nbins must be 1 to %d", kMaxBins);
     if (!(dx > 0.0)) return set_error(LF2_ERR_INVALID, "dx must be > 0");
     const int n = n3[0];
@@ -100,31 +107,44 @@ extern "C" lf2_status lf2_power_spectrum(lf2_field f, int comp, int nbins, doubl
     if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)3 * nbins * sizeof(double));
     if (e != cudaSuccess) st = cuda_error(e, "spectrum buffers");
     if (st == LF2_OK) {
-        const int g = (int)((sites + 255) / 256 < 152 * 16 ? (sites + 255) / 256 : 152 * 16);
-        if (dbl)
-            k_extract<double><<<g, 256, 0, s>>>((const double *)f->val[f->front], (double *)real, sites, f->ncomp, comp);
-        else
-            k_extract<float><<<g, 256, 0, s>>>((const float *)f->val[f->front], (float *)real, sites, f->ncomp, comp);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) st = cuda_error(e, "component copy");
-    }
-    if (st == LF2_OK) {
         cufftResult r = cufftPlan3d(&plan, n, n, n, dbl ? CUFFT_D2Z : CUFFT_R2C);
         have_plan = r == CUFFT_SUCCESS;
         if (r == CUFFT_SUCCESS) r = cufftSetStream(plan, s);
-        if (r == CUFFT_SUCCESS)
-            r = dbl ? cufftExecD2Z(plan, (cufftDoubleReal *)real, (cufftDoubleComplex *)spec)
-                    : cufftExecR2C(plan, (cufftReal *)real, (cufftComplex *)spec);
         if (r != CUFFT_SUCCESS) st = set_error(r == CUFFT_ALLOC_FAILED ? LF2_ERR_NOMEM : LF2_ERR_CUDA, "cuFFT error %d", (int)r);
     }
-    if (st == LF2_OK) {
-        const double kunit = 2.0 * M_PI / (n * dx);
-        const double inv_volume = 1.0 / ((double)n * n * n);
-        const size_t smem = (size_t)3 * nbins * sizeof(double);
+    // one component, or every component in order with their powers added bin by bin
+    const int c0 = comp < 0 ? 0 : comp, c1 = comp < 0 ? f->ncomp : comp + 1;
+    const double kunit = 2.0 * M_PI / (n * dx);
+    const double inv_volume = 1.0 / ((double)n * n * n);
+    const size_t smem = (size_t)3 * nbins * sizeof(double);
+    for (int c = c0; c < c1 && st == LF2_OK; ++c) {
+        const int g = (int)((sites + 255) / 256 < 152 * 16 ? (sites + 255) / 256 : 152 * 16);
         if (dbl)
-            k_bin<double2><<<kBinBlocks, kBinThreads, smem, s>>>((const double2 *)spec, n, nbins, kunit, inv_volume, partials);
+            k_extract<double><<<g, 256, 0, s>>>((const double *)f->val[f->front], (double *)real, sites, f->ncomp, c);
         else
-            k_bin<float2><<<kBinBlocks, kBinThreads, smem, s>>>((const float2 *)spec, n, nbins, kunit, inv_volume, partials);
+            k_extract<float><<<g, 256, 0, s>>>((const float *)f->val[f->front], (float *)real, sites, f->ncomp, c);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            st = cuda_error(e, "component copy");
+            break;
+        }
+        const cufftResult r = dbl ? cufftExecD2Z(plan, (cufftDoubleReal *)real, (cufftDoubleComplex *)spec)
+                                  : cufftExecR2C(plan, (cufftReal *)real, (cufftComplex *)spec);
+        if (r != CUFFT_SUCCESS) {
+            st = set_error(LF2_ERR_CUDA, "cuFFT error %d", (int)r);
+            break;
+        }
+        const int add = c > c0;
+        if (dbl)
+            k_bin<double2><<<kBinBlocks, kBinThreads, smem, s>>>((const double2 *)spec, n, nbins, kunit, inv_volume, partials,
+                                                                 add);
+        else
+            k_bin<float2><<<kBinBlocks, kBinThreads, smem, s>>>((const float2 *)spec, n, nbins, kunit, inv_volume, partials,
+                                                                add);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_error(e, "binning");
+    }
+    if (st == LF2_OK) {
         k_bin_final<<<(3 * nbins + 255) / 256, 256, 0, s>>>(partials, kBinBlocks, nbins, out);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(power, out, nbins * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -193,7 +193,8 @@ def lf2_field_read(f, path, which=0, stream=None):
 
 
 def lf2_power_spectrum(f, comp=0, nbins=32, dx=1.0, stream=None):
-    """(mean power, mean |k|, mode count) per shell b = floor(|m|), as numpy arrays."""
+    """(mean power, mean |k|, mode count) per shell b = floor(|m|), as numpy arrays; comp = -1 sums
+    the components' powers."""
     power, kmean, count = np.zeros(nbins), np.zeros(nbins), np.zeros(nbins)
     dp = ctypes.POINTER(ctypes.c_double)
     _call("lf2_power_spectrum", f, int(comp), int(nbins), float(dx), power.ctypes.data_as(dp),

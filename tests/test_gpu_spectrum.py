@@ -22,7 +22,10 @@ def lf2():
 
 
 @pytest.mark.parametrize("prec,n,ncomp,comp,tol", [("f64", 16, 2, 1, 1e-12), ("f32", 20, 1, 0, 1e-5),
-                                                   ("f64", 15, 1, 0, 1e-12)])
+                                                   ("f64", 15, 1, 0, 1e-12),
+                                                   # comp = -1: the components' powers summed
+                                                   ("f64", 16, 2, -1, 1e-12), ("f32k", 12, 3, -1, 1e-5),
+                                                   ("f64", 10, 6, -1, 1e-12)])
 def test_spectrum_matches_oracle(lf2, ora, prec, n, ncomp, comp, tol):
     phi = inputs.gaussian_field(n, n, n, ncomp, sigma=1.0, seed=141)
     nbins = 20
@@ -41,6 +44,11 @@ def test_spectrum_rejects_non_cubic(lf2):
         with pytest.raises(lf2.LF2Error) as e:
             lf2.lf2_power_spectrum(s.phi)
         assert e.value.status == lf2.LF2_ERR_UNSUPPORTED
+    with lf2.System((8, 8, 8), 2, "f64") as s:
+        for comp in (-2, 2):
+            with pytest.raises(lf2.LF2Error) as e:
+                lf2.lf2_power_spectrum(s.phi, comp=comp)
+            assert e.value.status == lf2.LF2_ERR_INVALID, comp
 
 
 def test_grf_initial_condition_has_the_requested_spectrum(lf2):

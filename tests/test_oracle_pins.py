@@ -410,5 +410,17 @@ def test_power_spectrum_parseval_and_plane_wave(ora):
     b = math.isqrt(sum(m * m for m in modes))
     assert P[b] * n[b] == pytest.approx(N ** 3 * A * A / 2, rel=1e-12)
     assert np.sum(P * n) == pytest.approx(N ** 3 * A * A / 2, rel=1e-12)
+    # all components (comp = -1): Parseval over both components, and for a complex field the
+    # shell means of |FFT(re + i im)|^2 / V (one complex transform, an independent route: the
+    # cross terms of the two components cancel between k and -k, which share a shell)
+    P, K, n = ora.power_spectrum(phi, comp=-1, nbins=64)
+    assert np.sum(P * n) == pytest.approx(np.sum(phi ** 2), rel=1e-12)
+    Z = np.abs(np.fft.fftn(phi[..., 0] + 1j * phi[..., 1])) ** 2 / N ** 3
+    m = np.fft.fftfreq(N) * N
+    shell = np.floor(np.sqrt(m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2) + 1e-9).astype(int)
+    for b in range(int(shell.max()) + 1):
+        sel = shell == b
+        assert n[b] == sel.sum(), b
+        assert P[b] == pytest.approx(Z[sel].mean(), rel=1e-12), b
     # mode counts of the first shells of an 8^3 lattice: |m|^2 = 0 | 1,2,3 | 4..8 ...
     assert n[0] == 1 and n[1] == 6 + 12 + 8
