@@ -56,7 +56,7 @@ typedef enum {
     LF2_ERR_UNSUPPORTED = 2, /* valid in the paper's model but not built: dim != 3, ncomp > 2 */
     LF2_ERR_NOMEM = 3,       /* a device or host allocation failed */
     LF2_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
-    LF2_ERR_TIMEOUT = 5,     /* reserved for a bounded device-side wait that gave up; no call returns it */
+    LF2_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (reported by lf2_field_check) */
     LF2_ERR_STATE = 6        /* call not allowed in the object's current state */
 } lf2_status;
 
@@ -206,7 +206,10 @@ lf2_status lf2_leapfrog_init(lf2_field phi, lf2_field pi, const lf2_params *p, v
 /* nsteps >= 0 leapfrog steps.  On entry phi holds phi_n and pi holds pi_{n-1/2}; on return
  * phi holds phi_{n+nsteps} and pi holds pi_{n+nsteps-1/2}.  phi's front and back buffers swap
  * after each step (no copy).  Uses the tuned kernel of lf2_tune when one was chosen for this
- * shape, else the default one; results are bitwise identical whichever kernel runs. */
+ * shape, else the default one; results are bitwise identical whichever kernel runs.  The
+ * environment variable LF2_TUNE changes that: "off" ignores tuned plans, "force" tunes a shape
+ * that has no plan on its first call (that call synchronises and allocates, so keep it out of
+ * stream capture). */
 lf2_status lf2_leapfrog(lf2_field phi, lf2_field pi, const lf2_params *p, int nsteps, void *stream);
 
 /* lf2_leapfrog with an explicit kernel choice (testing and tuning).  LF2_ERR_UNSUPPORTED if the
@@ -240,7 +243,7 @@ lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, d
  * grid barrier between steps; larger ones run one launch per step.  Results are the same bits
  * either way.  A barrier that does not complete within about a second (all blocks of a
  * cooperative launch are resident, so it always completes) ends the run and leaves NaN in the
- * records from that step on.  Enqueues on `stream` without waiting; after the first call on phi (which may
+ * records from that step on; lf2_field_check(phi) then returns LF2_ERR_TIMEOUT.  Enqueues on `stream` without waiting; after the first call on phi (which may
  * allocate its back buffer and energy scratch, so make it outside a stream capture) calls
  * allocate nothing and can be captured into a CUDA graph.  Calls on one phi share its energy
  * scratch with lf2_energy and lf2_energy_device: order them on one stream.
@@ -260,6 +263,14 @@ lf2_status lf2_leapfrog_energy(lf2_field phi, lf2_field pi, const lf2_params *p,
  * `which` outside 0..3 or an unknown ref_prec; LF2_ERR_STATE if that buffer does not exist. */
 lf2_status lf2_field_compare(lf2_field f, int which, const void *ref, lf2_precision ref_prec, double *out,
                              void *stream);
+
+/* Status of the last multi-step lf2_leapfrog_energy run on phi: LF2_ERR_TIMEOUT (once; the
+ * flag is then cleared) if one of its grid barriers gave up, else LF2_OK.  The paper has no
+ * counterpart (its programs have no device-side waits).  Synchronises `stream`.  Host-side
+ * failure injection for tests: with LF2_FAULT=timeout in the environment the barrier waits give
+ * up at once; with LF2_FAULT=launch, lf2_leapfrog and lf2_leapfrog_energy return LF2_ERR_CUDA
+ * without launching; with LF2_FAULT=alloc, the library's allocations fail with LF2_ERR_NOMEM. */
+lf2_status lf2_field_check(lf2_field phi, void *stream);
 
 /* lf2_energy for callers that cannot allocate device memory.  The paper has no counterpart;
  * this entry point exists for callers whose device allocator belongs to someone else (a memory

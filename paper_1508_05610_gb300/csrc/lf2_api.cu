@@ -96,6 +96,15 @@ bool fault_injected(const char *what) {
     return f && !strcmp(f, what);
 }
 
+// LF2_TUNE: "off" -- lf2_leapfrog ignores tuned plans; "force" -- it tunes a shape without a
+// plan on first use; unset or anything else -- it uses a plan once lf2_tune made one.
+TuneMode tune_mode() {
+    const char *t = getenv("LF2_TUNE");
+    if (t && !strcmp(t, "off")) return TuneMode::Off;
+    if (t && !strcmp(t, "force")) return TuneMode::Force;
+    return TuneMode::On;
+}
+
 lf2_status alloc_back(lf2_field f, const char *what) {
     if (f->val[1 - f->front]) return LF2_OK;
     if (fault_injected("alloc")) return fail(LF2_ERR_NOMEM, "allocation failure injected by LF2_FAULT=alloc");
@@ -430,10 +439,19 @@ lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int
     cudaStream_t s = (cudaStream_t)stream;
     int kernel = cfg ? cfg->kernel : LF2_KERNEL_AUTO;
     if (kernel < LF2_KERNEL_AUTO || kernel > LF2_KERNEL_TBLOCK) return fail(LF2_ERR_INVALID, "unknown kernel %d", kernel);
+    if (fault_injected("launch")) return fail(LF2_ERR_CUDA, "launch failure injected by LF2_FAULT=launch");
     lf2_step_config tuned{};
-    if (kernel == LF2_KERNEL_AUTO && plan_lookup(phi->lat->n, phi->ncomp, phi->prec, &tuned)) {
-        cfg = &tuned;
-        kernel = tuned.kernel;
+    if (kernel == LF2_KERNEL_AUTO && tune_mode() != TuneMode::Off) {
+        bool have = plan_lookup(phi->lat->n, phi->ncomp, phi->prec, &tuned);
+        if (!have && tune_mode() == TuneMode::Force) {
+            st = lf2_tune(phi, pi, p, 0, &tuned, stream);
+            if (st != LF2_OK) return st;
+            have = true;
+        }
+        if (have) {
+            cfg = &tuned;
+            kernel = tuned.kernel;
+        }
     }
     const int tile_y = cfg ? cfg->tile_y : 0;
     const int zchunk = cfg ? cfg->zchunk : 0;
@@ -524,13 +542,14 @@ lf2_status lf2_leapfrog_energy(lf2_field phi, lf2_field pi, const lf2_params *p,
     if (st != LF2_OK) return st;
     if (nsteps < 0) return fail(LF2_ERR_INVALID, "nsteps must be >= 0");
     if (nsteps > 0 && !dev_records) return fail(LF2_ERR_INVALID, "records pointer is NULL");
+    if (nsteps > 0 && fault_injected("launch")) return fail(LF2_ERR_CUDA, "launch failure injected by LF2_FAULT=launch");
     cudaStream_t s = (cudaStream_t)stream;
     st = ensure_dynamic(phi, s);
     if (st == LF2_OK) st = ensure_energy_scratch(phi);
     if (st != LF2_OK) return st;
     // small lattices: all steps in one cooperative launch (bitwise the per-step launches)
     const cudaError_t e = launch_steps_energy(step_args(phi, pi, p, p->dt, true), nsteps, phi->energy_scratch,
-                                              dev_records, s);
+                                              dev_records, fault_injected("timeout"), s);
     if (e == cudaSuccess) {
         if (nsteps & 1) phi->front = 1 - phi->front;
         return LF2_OK;
@@ -565,6 +584,18 @@ lf2_status lf2_field_compare(lf2_field f, int which, const void *ref, lf2_precis
              "compare copy");
     LF2_CUDA(cudaStreamSynchronize(s), "compare sync");
     memcpy(out, f->energy_host, 4 * sizeof(double));
+    return LF2_OK;
+}
+
+lf2_status lf2_field_check(lf2_field phi, void *stream) {
+    if (!phi) return fail(LF2_ERR_INVALID, "field is NULL");
+    if (!phi->energy_scratch) return LF2_OK;  // no multi-step run yet
+    bool timed_out = false;
+    LF2_CUDA(steps_energy_timed_out(phi->energy_scratch, &timed_out, (cudaStream_t)stream), "status read");
+    if (timed_out)
+        return fail(LF2_ERR_TIMEOUT,
+                    "a grid barrier of the last multi-step lf2_leapfrog_energy run gave up: its records from that step "
+                    "on are NaN and the fields are not a valid state");
     return LF2_OK;
 }
 

@@ -301,8 +301,9 @@ constexpr size_t kBarrierOffset = (size_t)(kEnergyBlocks - 1) * kEnergySlots;
 // cooperative launch guarantees, keeps real waits to microseconds.
 constexpr unsigned kBarrierPolls = 1u << 24;
 
-// Grid barrier with a bounded wait: false if the wait ran out here or in another block.
-__device__ __forceinline__ bool grid_sync(unsigned *bar) {
+// Grid barrier with a bounded wait (`polls` polls): false if the wait ran out here or in
+// another block.
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned polls_max) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -317,7 +318,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar) {
         } else {
             unsigned polls = 0;
             while (*gen == g) {
-                if (++polls > kBarrierPolls) {
+                if (++polls > polls_max) {
                     atomicExch(bar + 2, 1u);
                     ok = 0;
                     break;
@@ -343,7 +344,7 @@ __device__ __forceinline__ void poison_records(double *records, int from, int ns
 template <int NC>
 __global__ void __launch_bounds__(kEnergyThreads)
     k_steps_energy_f64(double *phi_a, double *phi_b, double *__restrict__ pi, Geom g, Coef64 k, CoefE ke, int nsteps,
-                       double *__restrict__ scratch, double *__restrict__ records) {
+                       double *__restrict__ scratch, double *__restrict__ records, unsigned polls) {
     constexpr int NS = kNs<NC>;
     __shared__ double sh[NS][kEnergyThreads];
     unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(kEnergyThreads)
             block_sum<NS>(acc, sh);
             if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
         }
-        if (!grid_sync(bar)) {
+        if (!grid_sync(bar, polls)) {
             poison_records(records, step, nsteps);
             return;
         }
@@ -373,7 +374,8 @@ __global__ void __launch_bounds__(kEnergyThreads)
 template <int NC, bool KAHAN>
 __global__ void __launch_bounds__(kEnergyThreads)
     k_steps_energy_f32(float *phi_a, float *phi_b, float *__restrict__ pi, float *__restrict__ comp, Geom g, Coef32 k,
-                       CoefE ke, int nsteps, double *__restrict__ scratch, double *__restrict__ records) {
+                       CoefE ke, int nsteps, double *__restrict__ scratch, double *__restrict__ records,
+                       unsigned polls) {
     constexpr int NS = kNs<NC>;
     __shared__ double sh[NS][kEnergyThreads];
     unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kEnergyThreads)
             block_sum<NS>(acc, sh);
             if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
         }
-        if (!grid_sync(bar)) {
+        if (!grid_sync(bar, polls)) {
             poison_records(records, step, nsteps);
             return;
         }
@@ -540,37 +542,52 @@ cudaError_t launch_cooperative(K kern, int nb, cudaStream_t s, Args... args) {
 // nb site blocks plus the reducing block
 template <int NC>
 cudaError_t steps_energy_nc(const StepArgs &a, int nsteps, int nb, const CoefE &ke, double *scratch, double *records,
-                            cudaStream_t s) {
+                            unsigned polls, cudaStream_t s) {
     nb += 1;
     if (a.prec == LF2_F64)
         return launch_cooperative(k_steps_energy_f64<NC>, nb, s, (double *)a.phi, (double *)a.phi_out, (double *)a.pi,
-                                  a.g, make_coef64(a.p, a.dt), ke, nsteps, scratch, records);
+                                  a.g, make_coef64(a.p, a.dt), ke, nsteps, scratch, records, polls);
     const Coef32 k = make_coef32(a.p, a.dt);
     if (a.prec == LF2_F32_KAHAN)
         return launch_cooperative(k_steps_energy_f32<NC, true>, nb, s, (float *)a.phi, (float *)a.phi_out,
-                                  (float *)a.pi, a.comp, a.g, k, ke, nsteps, scratch, records);
+                                  (float *)a.pi, a.comp, a.g, k, ke, nsteps, scratch, records, polls);
     return launch_cooperative(k_steps_energy_f32<NC, false>, nb, s, (float *)a.phi, (float *)a.phi_out, (float *)a.pi,
-                              a.comp, a.g, k, ke, nsteps, scratch, records);
+                              a.comp, a.g, k, ke, nsteps, scratch, records, polls);
 }
 
 }  // namespace
 
-cudaError_t launch_steps_energy(const StepArgs &a, int nsteps, double *scratch, double *records, cudaStream_t s) {
+cudaError_t launch_steps_energy(const StepArgs &a, int nsteps, double *scratch, double *records, bool no_wait,
+                                cudaStream_t s) {
     const int nb = energy_grid(a.g.sites);  // site blocks, as for one launch per step
     if (!a.drift || nsteps < 2 || nb > kStepsMaxBlocks) return cudaErrorNotSupported;
     // the barrier's arrival count, generation and error flag start at zero
     cudaError_t e = cudaMemsetAsync(scratch + kBarrierOffset, 0, 4 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const CoefE ke = make_coefE(a.p);
+    const unsigned polls = no_wait ? 0u : kBarrierPolls;
     switch (a.ncomp) {
-        case 1: return steps_energy_nc<1>(a, nsteps, nb, ke, scratch, records, s);
-        case 2: return steps_energy_nc<2>(a, nsteps, nb, ke, scratch, records, s);
-        case 3: return steps_energy_nc<3>(a, nsteps, nb, ke, scratch, records, s);
-        case 4: return steps_energy_nc<4>(a, nsteps, nb, ke, scratch, records, s);
-        case 5: return steps_energy_nc<5>(a, nsteps, nb, ke, scratch, records, s);
-        case 6: return steps_energy_nc<6>(a, nsteps, nb, ke, scratch, records, s);
+        case 1: return steps_energy_nc<1>(a, nsteps, nb, ke, scratch, records, polls, s);
+        case 2: return steps_energy_nc<2>(a, nsteps, nb, ke, scratch, records, polls, s);
+        case 3: return steps_energy_nc<3>(a, nsteps, nb, ke, scratch, records, polls, s);
+        case 4: return steps_energy_nc<4>(a, nsteps, nb, ke, scratch, records, polls, s);
+        case 5: return steps_energy_nc<5>(a, nsteps, nb, ke, scratch, records, polls, s);
+        case 6: return steps_energy_nc<6>(a, nsteps, nb, ke, scratch, records, polls, s);
         default: return cudaErrorNotSupported;
     }
+}
+
+cudaError_t steps_energy_timed_out(double *scratch, bool *out, cudaStream_t s) {
+    unsigned word[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(word, scratch + kBarrierOffset, sizeof word, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *out = word[2] != 0u;
+    if (*out) {
+        e = cudaMemsetAsync(scratch + kBarrierOffset, 0, sizeof word, s);  // reported once
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return e;
 }
 
 cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool ref_double, long long n,

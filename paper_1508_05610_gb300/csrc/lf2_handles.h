@@ -38,6 +38,12 @@ namespace lf2 {
 lf2_status set_error(lf2_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 lf2_status cuda_error(cudaError_t e, const char *what);
 
+// Host-side switches (lf2_api.cu): LF2_FAULT=<what> injects a failure; LF2_TUNE picks how
+// lf2_leapfrog uses tuned plans.
+bool fault_injected(const char *what);
+enum class TuneMode { Off, On, Force };
+TuneMode tune_mode();
+
 // Field helpers (lf2_api.cu).
 lf2_status ensure_dynamic(lf2_field phi, cudaStream_t s);               // phi back buffer (+ compensation)
 lf2_status ensure_tblock(lf2_field phi, lf2_field pi, cudaStream_t s);  // + pi and compensation back buffers

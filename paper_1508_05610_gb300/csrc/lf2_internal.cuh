@@ -50,7 +50,12 @@ cudaError_t launch_step_energy(const StepArgs &a, double *scratch, double *recor
 // records[0 .. nsteps) and leaving phi in a.phi_out if nsteps is odd, else in a.phi;
 // cudaErrorNotSupported (nothing launched) unless the lattice is small enough for every block
 // of the reduction grid to be resident at once and nsteps >= 2.  Bitwise the per-step launches.
-cudaError_t launch_steps_energy(const StepArgs &a, int nsteps, double *scratch, double *records, cudaStream_t s);
+// no_wait: the grid barrier gives up at once (host-side timeout injection, LF2_FAULT=timeout).
+cudaError_t launch_steps_energy(const StepArgs &a, int nsteps, double *scratch, double *records, bool no_wait,
+                                cudaStream_t s);
+// Whether the last multi-step run on this scratch had a barrier give up (the flag is then
+// cleared); synchronises `s`.
+cudaError_t steps_energy_timed_out(double *scratch, bool *out, cudaStream_t s);
 
 // Temporal blocking: `depth` fused steps per pass over x-y tiles of tile_x x tile_y output
 // sites (plus a depth-site halo), z-chunks of `zchunk` planes.  Unlike the one-step kernels it

@@ -80,6 +80,7 @@ SIGNATURES = {
     "lf2_energy_device": [_vp, _vp, ctypes.POINTER(lf2_params), _vp, _vp],
     "lf2_energy_noalloc": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
     "lf2_leapfrog_energy": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, _vp, _vp],
+    "lf2_field_check": [_vp, _vp],
     "lf2_field_compare": [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp],
     "lf2_ensemble_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(lf2_params),
                             ctypes.POINTER(_vp)],
@@ -239,6 +240,12 @@ def lf2_leapfrog_energy(phi, pi, p: lf2_params, nsteps, dev_records_ptr, stream=
     """nsteps leapfrog steps, one kernel each, that also write the energy record of the state at
     the start of every step (nsteps x 16 doubles of device memory at dev_records_ptr)."""
     _call("lf2_leapfrog_energy", phi, pi, ctypes.byref(p), int(nsteps), dev_records_ptr, _stream_ptr(stream))
+
+
+def lf2_field_check(f, stream=None):
+    """Raises LF2Error (LF2_ERR_TIMEOUT) if a grid barrier of the last multi-step
+    lf2_leapfrog_energy run on f gave up."""
+    _call("lf2_field_check", f, _stream_ptr(stream))
 
 
 def lf2_field_compare(f, ref_ptr, ref_prec, which=0, stream=None) -> dict:

@@ -144,6 +144,29 @@ def test_alloc_failure_is_reported_not_hidden(lib, monkeypatch):
         lib.lf2_lattice_destroy(lat)
 
 
+def test_injected_launch_failure_is_reported_before_any_device_call(lib, monkeypatch):
+    """LF2_FAULT=launch: the stepping calls report LF2_ERR_CUDA without launching (checked here
+    with borrowed, never-dereferenced pointers and no GPU); lf2_field_check on a field that has
+    run nothing reports LF2_OK without a device call."""
+    monkeypatch.setenv("LF2_FAULT", "launch")
+    lat = lib.lf2_lattice_create([4, 4, 4])
+    try:
+        f = lib.lf2_field_wrap(lat, 1, lib.LF2_F64, [0x1000])
+        g = lib.lf2_field_wrap(lat, 1, lib.LF2_F64, [0x2000])
+        p = lib.params()
+        try:
+            for call in (lambda: lib.lf2_leapfrog(f, g, p, 3), lambda: lib.lf2_leapfrog_energy(f, g, p, 3, 0x3000)):
+                with pytest.raises(lib.LF2Error) as e:
+                    call()
+                assert e.value.status == lib.LF2_ERR_CUDA and "LF2_FAULT=launch" in str(e.value)
+            lib.lf2_field_check(f)
+        finally:
+            lib.lf2_field_free(f)
+            lib.lf2_field_free(g)
+    finally:
+        lib.lf2_lattice_destroy(lat)
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1508_05610_gb300")
     for dirpath, _, files in os.walk(pkg):

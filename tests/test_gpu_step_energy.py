@@ -169,3 +169,38 @@ def test_fused_energy_argument_errors(lf2):
         r = rec[0].cpu().numpy()
         assert r[0] == 0.0 and r[1] == 0.0 and r[2] == 0.25 * 512 and r[3] == 0.25 * 512
         assert np.all(r[4:] == 0.0)
+
+
+def test_barrier_timeout_is_reported_and_the_context_stays_usable(lf2, ora, monkeypatch):
+    """Failure detection without a GPU fault: LF2_FAULT=timeout makes every grid-barrier wait of
+    the multi-step kernel give up at once.  The run ends by itself, its last records are NaN,
+    lf2_field_check reports LF2_ERR_TIMEOUT once, and a normal run right after on the same
+    field gives the oracle's energies."""
+    import torch
+    kw = dict(dx=1.0, dt=0.1, lam=1.0, eta=1.0, m2=0.0)
+    p = lf2.params(**kw)
+    phi0 = inputs.gaussian_field(16, 16, 16, 1, sigma=0.1, seed=inputs.BASE_SEED + 5)
+    steps = 6
+    rec = torch.zeros((steps, 16), dtype=torch.float64, device="cuda")
+    with lf2.System((16, 16, 16), 1, "f64") as s:
+        s.upload(phi0, np.zeros_like(phi0))
+        lf2.lf2_leapfrog_init(s.phi, s.pi, p)
+        monkeypatch.setenv("LF2_FAULT", "timeout")
+        lf2.lf2_leapfrog_energy(s.phi, s.pi, p, steps, rec.data_ptr())
+        monkeypatch.delenv("LF2_FAULT")
+        with pytest.raises(lf2.LF2Error) as e:
+            lf2.lf2_field_check(s.phi)
+        assert e.value.status == lf2.LF2_ERR_TIMEOUT
+        lf2.lf2_field_check(s.phi)  # reported once
+        assert torch.isnan(rec[-1]).all()
+        # the same field and context, a clean run
+        s.upload(phi0, np.zeros_like(phi0))
+        lf2.lf2_leapfrog_init(s.phi, s.pi, p)
+        lf2.lf2_leapfrog_energy(s.phi, s.pi, p, steps, rec.data_ptr())
+        lf2.lf2_field_check(s.phi)
+        got = rec.cpu().numpy()
+    ophi, opi = ora.evolve(phi0, np.zeros_like(phi0), 0, half_kick=True, **kw)
+    for n in range(steps):
+        oe = ora.energy(ophi, opi, **kw)
+        assert abs(got[n, 3] - oe["total"]) <= F64_TOL * abs(oe["total"]), n
+        ophi, opi = ora.evolve(ophi, opi, 1, **kw)

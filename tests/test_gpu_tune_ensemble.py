@@ -54,6 +54,33 @@ def test_tune_leaves_fields_untouched_and_plan_is_bitwise(lf2, prec, ncomp):
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), plan
 
 
+def test_tune_env_force_tunes_on_first_use_and_off_ignores_plans(lf2, monkeypatch):
+    """LF2_TUNE=force: lf2_leapfrog on a shape without a plan tunes it first (a plan exists
+    afterwards); LF2_TUNE=off: the default kernel runs; both step bitwise like the site kernel."""
+    shape, ncomp, prec = (42, 22, 18), 1, "f32k"  # a shape no other test tunes
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    p = lf2.params(**kw)
+    phi0 = inputs.gaussian_field(*shape, ncomp, sigma=0.4, seed=63)
+    ref = run_site(lf2, shape, ncomp, prec, phi0, np.zeros_like(phi0), kw, 9)
+
+    def plan():
+        try:
+            return lf2.lf2_tune_lookup(shape, ncomp, lf2.PRECISIONS[prec])
+        except lf2.LF2Error as e:
+            assert e.status == lf2.LF2_ERR_STATE
+            return None
+    assert plan() is None
+    for mode in ("off", "force"):
+        monkeypatch.setenv("LF2_TUNE", mode)
+        with lf2.System(shape, ncomp, prec) as s:
+            s.upload(phi0, np.zeros_like(phi0))
+            lf2.lf2_leapfrog(s.phi, s.pi, p, 9)  # as run_site: no half-kick
+            got = s.download()
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), mode
+        planned = plan()
+        assert (planned is None) == (mode == "off"), (mode, planned)
+
+
 def test_tune_cache_file_is_read_by_a_fresh_process(lf2, tmp_path):
     cache = tmp_path / "plans.txt"
     code = r"""
