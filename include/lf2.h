@@ -272,6 +272,14 @@ lf2_status lf2_field_compare(lf2_field f, int which, const void *ref, lf2_precis
  * without launching; with LF2_FAULT=alloc, the library's allocations fail with LF2_ERR_NOMEM. */
 lf2_status lf2_field_check(lf2_field phi, void *stream);
 
+/* Index checks of a debug build, an aid for the kernels' index arithmetic (the paper has no
+ * counterpart).  The library built with -DLF2_DEBUG_BOUNDS
+ * (lib/liblf2_debug.so) checks every element index the leapfrog, temporal-blocking, ensemble
+ * and energy kernels compute against its allocation, replaces an index outside by a safe one
+ * and counts it.  Writes the count since the last reset to *violations (reset != 0 clears it);
+ * synchronises the device.  The release library returns LF2_ERR_UNSUPPORTED (*violations = 0). */
+lf2_status lf2_debug_bounds(unsigned long long *violations, int reset);
+
 /* lf2_energy for callers that cannot allocate device memory.  The paper has no counterpart;
  * this entry point exists for callers whose device allocator belongs to someone else (a memory
  * pool or host framework that forbids cudaMalloc while it runs) or that must make no

@@ -599,6 +599,27 @@ lf2_status lf2_field_check(lf2_field phi, void *stream) {
     return LF2_OK;
 }
 
+lf2_status lf2_debug_bounds(unsigned long long *violations, int reset) {
+    if (!violations) return fail(LF2_ERR_INVALID, "NULL argument");
+#ifdef LF2_DEBUG_BOUNDS
+    using Fn = cudaError_t (*)(unsigned long long *, bool);
+    const Fn units[] = {bounds_violations_site,        bounds_violations_stream,       bounds_violations_tblock_f64,
+                        bounds_violations_tblock_f32k, bounds_violations_tblock_f32, bounds_violations_energy};
+    unsigned long long total = 0;
+    for (Fn f : units) {
+        unsigned long long n = 0;
+        LF2_CUDA(f(&n, reset != 0), "bounds counter");
+        total += n;
+    }
+    *violations = total;
+    return LF2_OK;
+#else
+    (void)reset;
+    *violations = 0;
+    return fail(LF2_ERR_UNSUPPORTED, "built without LF2_DEBUG_BOUNDS (build the debug library to count index violations)");
+#endif
+}
+
 lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream) {
     lf2_status st = check_pair(phi, pi);
     if (st == LF2_OK) st = check_params(p);

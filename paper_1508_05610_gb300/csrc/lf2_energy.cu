@@ -20,6 +20,7 @@
 // arithmetic, give bitwise the record of the stand-alone reduction.
 #include <mutex>
 
+#include "lf2_bounds.cuh"
 #include "lf2_internal.cuh"
 
 namespace lf2 {
@@ -43,9 +44,10 @@ __device__ __forceinline__ R ld_field(const R *p) {
 }
 
 template <typename R, int NC, bool COHERENT = false>
-__device__ __forceinline__ void load_d(const R *__restrict__ f, long long s, double (&v)[NC]) {
+__device__ __forceinline__ void load_d(const R *__restrict__ f, long long s, long long sites, double (&v)[NC]) {
+    const long long i = checked(s * NC, NC, sites * NC);
 #pragma unroll
-    for (int a = 0; a < NC; ++a) v[a] = (double)ld_field<COHERENT>(f + s * NC + a);
+    for (int a = 0; a < NC; ++a) v[a] = (double)ld_field<COHERENT>(f + i + a);
 }
 
 // Adds one site's raw sums to acc.  c: phi_n at the site, xm..zp: its neighbours in the order
@@ -172,14 +174,14 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energy(const R *__restrict__
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride) {
         const Nbr n = neighbours(s, g);
         double c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC];
-        load_d<R, NC>(phi, s, c);
-        load_d<R, NC>(phi, n.xm, xm);
-        load_d<R, NC>(phi, n.xp, xp);
-        load_d<R, NC>(phi, n.ym, ym);
-        load_d<R, NC>(phi, n.yp, yp);
-        load_d<R, NC>(phi, n.zm, zm);
-        load_d<R, NC>(phi, n.zp, zp);
-        load_d<R, NC>(pi, s, p);
+        load_d<R, NC>(phi, s, g.sites, c);
+        load_d<R, NC>(phi, n.xm, g.sites, xm);
+        load_d<R, NC>(phi, n.xp, g.sites, xp);
+        load_d<R, NC>(phi, n.ym, g.sites, ym);
+        load_d<R, NC>(phi, n.yp, g.sites, yp);
+        load_d<R, NC>(phi, n.zm, g.sites, zm);
+        load_d<R, NC>(phi, n.zp, g.sites, zp);
+        load_d<R, NC>(pi, s, g.sites, p);
         energy_site<NC>(c, xm, xp, ym, yp, zm, zp, p, acc, k);
     }
     finish_energy<NC>(acc, sh, scratch, k, record);
@@ -193,21 +195,22 @@ __device__ __forceinline__ void site_step_energy_f64(const double *__restrict__ 
                                                      const Coef64 &k, const CoefE &ke, double (&acc)[kNs<NC>]) {
     const Nbr n = neighbours(s, g);
     double c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], out[NC];
-    load_d<double, NC, COHERENT>(phi, s, c);
-    load_d<double, NC, COHERENT>(phi, n.xm, xm);
-    load_d<double, NC, COHERENT>(phi, n.xp, xp);
-    load_d<double, NC, COHERENT>(phi, n.ym, ym);
-    load_d<double, NC, COHERENT>(phi, n.yp, yp);
-    load_d<double, NC, COHERENT>(phi, n.zm, zm);
-    load_d<double, NC, COHERENT>(phi, n.zp, zp);
+    load_d<double, NC, COHERENT>(phi, s, g.sites, c);
+    load_d<double, NC, COHERENT>(phi, n.xm, g.sites, xm);
+    load_d<double, NC, COHERENT>(phi, n.xp, g.sites, xp);
+    load_d<double, NC, COHERENT>(phi, n.ym, g.sites, ym);
+    load_d<double, NC, COHERENT>(phi, n.yp, g.sites, yp);
+    load_d<double, NC, COHERENT>(phi, n.zm, g.sites, zm);
+    load_d<double, NC, COHERENT>(phi, n.zp, g.sites, zp);
+    const long long o = checked(s * NC, NC, g.sites * NC);
 #pragma unroll
-    for (int a = 0; a < NC; ++a) p[a] = pi[s * NC + a];
+    for (int a = 0; a < NC; ++a) p[a] = pi[o + a];
     energy_site<NC>(c, xm, xp, ym, yp, zm, zp, p, acc, ke);
     update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, out, k);
 #pragma unroll
     for (int a = 0; a < NC; ++a) {
-        pi[s * NC + a] = p[a];
-        phi_out[s * NC + a] = out[a];
+        pi[o + a] = p[a];
+        phi_out[o + a] = out[a];
     }
 }
 
@@ -219,18 +222,22 @@ __device__ __forceinline__ void site_step_energy_f32(const float *__restrict__ p
                                                      const Geom &g, const Coef32 &k, const CoefE &ke,
                                                      double (&acc)[kNs<NC>]) {
     const Nbr n = neighbours(s, g);
+    const long long cnt = g.sites * NC;
+    const long long o = checked(s * NC, NC, cnt), ixm = checked(n.xm * NC, NC, cnt), ixp = checked(n.xp * NC, NC, cnt),
+                    iym = checked(n.ym * NC, NC, cnt), iyp = checked(n.yp * NC, NC, cnt),
+                    izm = checked(n.zm * NC, NC, cnt), izp = checked(n.zp * NC, NC, cnt);
     float c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], out[NC];
 #pragma unroll
     for (int a = 0; a < NC; ++a) {
-        c[a] = ld_field<COHERENT>(phi + s * NC + a);
-        xm[a] = ld_field<COHERENT>(phi + n.xm * NC + a);
-        xp[a] = ld_field<COHERENT>(phi + n.xp * NC + a);
-        ym[a] = ld_field<COHERENT>(phi + n.ym * NC + a);
-        yp[a] = ld_field<COHERENT>(phi + n.yp * NC + a);
-        zm[a] = ld_field<COHERENT>(phi + n.zm * NC + a);
-        zp[a] = ld_field<COHERENT>(phi + n.zp * NC + a);
-        p[a] = pi[s * NC + a];
-        cm[a] = KAHAN ? comp[s * NC + a] : 0.0f;
+        c[a] = ld_field<COHERENT>(phi + o + a);
+        xm[a] = ld_field<COHERENT>(phi + ixm + a);
+        xp[a] = ld_field<COHERENT>(phi + ixp + a);
+        ym[a] = ld_field<COHERENT>(phi + iym + a);
+        yp[a] = ld_field<COHERENT>(phi + iyp + a);
+        zm[a] = ld_field<COHERENT>(phi + izm + a);
+        zp[a] = ld_field<COHERENT>(phi + izp + a);
+        p[a] = pi[o + a];
+        cm[a] = KAHAN ? comp[o + a] : 0.0f;
     }
     double dc[NC], dxm[NC], dxp[NC], dym[NC], dyp[NC], dzm[NC], dzp[NC], dp[NC];
 #pragma unroll
@@ -248,9 +255,9 @@ __device__ __forceinline__ void site_step_energy_f32(const float *__restrict__ p
     update_f32<NC, KAHAN>(c, xm, xp, ym, yp, zm, zp, p, cm, out, k);
 #pragma unroll
     for (int a = 0; a < NC; ++a) {
-        pi[s * NC + a] = p[a];
-        phi_out[s * NC + a] = out[a];
-        if (KAHAN) comp[s * NC + a] = cm[a];
+        pi[o + a] = p[a];
+        phi_out[o + a] = out[a];
+        if (KAHAN) comp[o + a] = cm[a];
     }
 }
 
@@ -589,6 +596,8 @@ cudaError_t steps_energy_timed_out(double *scratch, bool *out, cudaStream_t s) {
     }
     return e;
 }
+
+cudaError_t bounds_violations_energy(unsigned long long *n, bool reset) { return bounds_violations_here(n, reset); }
 
 cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool ref_double, long long n,
                            double *scratch, cudaStream_t s) {

@@ -112,6 +112,15 @@ static_assert(sizeof(lf2_energy_t) == kEnergySlots * sizeof(double), "energy rec
 cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool ref_double, long long n,
                            double *scratch, cudaStream_t s);
 
+// Index-check violations counted by each kernel translation unit of a -DLF2_DEBUG_BOUNDS build
+// (0 otherwise), optionally reset.
+cudaError_t bounds_violations_site(unsigned long long *n, bool reset);
+cudaError_t bounds_violations_stream(unsigned long long *n, bool reset);
+cudaError_t bounds_violations_tblock_f64(unsigned long long *n, bool reset);
+cudaError_t bounds_violations_tblock_f32k(unsigned long long *n, bool reset);
+cudaError_t bounds_violations_tblock_f32(unsigned long long *n, bool reset);
+cudaError_t bounds_violations_energy(unsigned long long *n, bool reset);
+
 // Fixed-size scratch of lf2_energy_noalloc (kEnergyScratchDoubles doubles, 78 KB), and the
 // doubles one reduction over `sites` sites uses (partial rows, record, counter).
 cudaError_t energy_noalloc_scratch(double **out);

@@ -6,6 +6,7 @@
 // index arithmetic instead of a stored halo).
 #include <type_traits>
 
+#include "lf2_bounds.cuh"
 #include "lf2_internal.cuh"
 
 namespace lf2 {
@@ -14,9 +15,10 @@ namespace {
 constexpr int kThreads = 256;
 
 template <typename R, int NC>
-__device__ __forceinline__ void load_site(const R *__restrict__ f, long long s, R (&v)[NC]) {
+__device__ __forceinline__ void load_site(const R *__restrict__ f, long long s, long long sites, R (&v)[NC]) {
+    const long long i = checked(s * NC, NC, sites * NC);
 #pragma unroll
-    for (int a = 0; a < NC; ++a) v[a] = __ldg(f + s * NC + a);
+    for (int a = 0; a < NC; ++a) v[a] = __ldg(f + i + a);
 }
 
 template <int NC>
@@ -31,20 +33,21 @@ __global__ void __launch_bounds__(kThreads) k_site_f64(const double *__restrict_
         const long long row = (long long)g.nx;
         const long long plane = row * g.ny;
         double c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], out[NC];
-        load_site<double, NC>(phi, s, c);
-        load_site<double, NC>(phi, s - x + wrap_dn(x, g.nx), xm);
-        load_site<double, NC>(phi, s - x + wrap_up(x, g.nx), xp);
-        load_site<double, NC>(phi, s + (wrap_dn(y, g.ny) - y) * row, ym);
-        load_site<double, NC>(phi, s + (wrap_up(y, g.ny) - y) * row, yp);
-        load_site<double, NC>(phi, s + (wrap_dn(z, g.nz) - z) * plane, zm);
-        load_site<double, NC>(phi, s + (wrap_up(z, g.nz) - z) * plane, zp);
+        const long long o = checked(s * NC, NC, g.sites * NC);
+        load_site<double, NC>(phi, s, g.sites, c);
+        load_site<double, NC>(phi, s - x + wrap_dn(x, g.nx), g.sites, xm);
+        load_site<double, NC>(phi, s - x + wrap_up(x, g.nx), g.sites, xp);
+        load_site<double, NC>(phi, s + (wrap_dn(y, g.ny) - y) * row, g.sites, ym);
+        load_site<double, NC>(phi, s + (wrap_up(y, g.ny) - y) * row, g.sites, yp);
+        load_site<double, NC>(phi, s + (wrap_dn(z, g.nz) - z) * plane, g.sites, zm);
+        load_site<double, NC>(phi, s + (wrap_up(z, g.nz) - z) * plane, g.sites, zp);
 #pragma unroll
-        for (int a = 0; a < NC; ++a) p[a] = pi[s * NC + a];
+        for (int a = 0; a < NC; ++a) p[a] = pi[o + a];
         update_f64<NC>(c, xm, xp, ym, yp, zm, zp, p, out, k);
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
-            pi[s * NC + a] = p[a];
-            if (drift) phi_out[s * NC + a] = out[a];
+            pi[o + a] = p[a];
+            if (drift) phi_out[o + a] = out[a];
         }
     }
 }
@@ -63,29 +66,30 @@ __global__ void __launch_bounds__(kThreads) k_site_f32(const float *__restrict__
         const long long row = (long long)g.nx;
         const long long plane = row * g.ny;
         float c[NC], xm[NC], xp[NC], ym[NC], yp[NC], zm[NC], zp[NC], p[NC], cm[NC], out[NC];
-        load_site<float, NC>(phi, s, c);
-        load_site<float, NC>(phi, s - x + wrap_dn(x, g.nx), xm);
-        load_site<float, NC>(phi, s - x + wrap_up(x, g.nx), xp);
-        load_site<float, NC>(phi, s + (wrap_dn(y, g.ny) - y) * row, ym);
-        load_site<float, NC>(phi, s + (wrap_up(y, g.ny) - y) * row, yp);
-        load_site<float, NC>(phi, s + (wrap_dn(z, g.nz) - z) * plane, zm);
-        load_site<float, NC>(phi, s + (wrap_up(z, g.nz) - z) * plane, zp);
+        const long long o = checked(s * NC, NC, g.sites * NC);
+        load_site<float, NC>(phi, s, g.sites, c);
+        load_site<float, NC>(phi, s - x + wrap_dn(x, g.nx), g.sites, xm);
+        load_site<float, NC>(phi, s - x + wrap_up(x, g.nx), g.sites, xp);
+        load_site<float, NC>(phi, s + (wrap_dn(y, g.ny) - y) * row, g.sites, ym);
+        load_site<float, NC>(phi, s + (wrap_up(y, g.ny) - y) * row, g.sites, yp);
+        load_site<float, NC>(phi, s + (wrap_dn(z, g.nz) - z) * plane, g.sites, zm);
+        load_site<float, NC>(phi, s + (wrap_up(z, g.nz) - z) * plane, g.sites, zp);
 #pragma unroll
-        for (int a = 0; a < NC; ++a) p[a] = pi[s * NC + a];
+        for (int a = 0; a < NC; ++a) p[a] = pi[o + a];
         if (MODE == 2) {
             kick_f32<NC>(c, xm, xp, ym, yp, zm, zp, p, k);
 #pragma unroll
-            for (int a = 0; a < NC; ++a) pi[s * NC + a] = p[a];
+            for (int a = 0; a < NC; ++a) pi[o + a] = p[a];
             continue;
         }
 #pragma unroll
-        for (int a = 0; a < NC; ++a) cm[a] = (MODE == 1) ? comp[s * NC + a] : 0.0f;
+        for (int a = 0; a < NC; ++a) cm[a] = (MODE == 1) ? comp[o + a] : 0.0f;
         update_f32<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, out, k);
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
-            pi[s * NC + a] = p[a];
-            phi_out[s * NC + a] = out[a];
-            if (MODE == 1) comp[s * NC + a] = cm[a];
+            pi[o + a] = p[a];
+            phi_out[o + a] = out[a];
+            if (MODE == 1) comp[o + a] = cm[a];
         }
     }
 }
@@ -109,6 +113,8 @@ __global__ void k_f32_to_f64(const float *__restrict__ src, double *__restrict__
 }
 
 }  // namespace
+
+cudaError_t bounds_violations_site(unsigned long long *n, bool reset) { return bounds_violations_here(n, reset); }
 
 template <int NC>
 void site_launch(const StepArgs &a, int grid, cudaStream_t s) {

@@ -11,6 +11,7 @@
 //
 // Requirements (else the one-thread-per-site kernel runs): rows of 16-byte multiples
 // (Nx * ncomp * sizeof(R) % 16 == 0) and Ny a multiple of the tile height.
+#include "lf2_bounds.cuh"
 #include "lf2_internal.cuh"
 
 namespace lf2 {
@@ -116,29 +117,33 @@ __global__ void __launch_bounds__(32 * BY) k_stream(const R *__restrict__ phi, R
     const long long off_l = (long long)y * rowE + (long long)xl * NC;
     const long long off_r = (long long)y * rowE + (long long)xr * NC;
 
+    const long long cnt = (long long)g.sites * NC;  // elements of every field buffer
     R below[E], cur[E], above[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) below[e] = cur[e] = above[e] = R(0);
     if (active) {
-        ld16<R, E>(phi + (long long)wrap_dn(z0, g.nz) * planeE + off_y, below);
-        ld16<R, E>(phi + (long long)z0 * planeE + off_y, cur);
+        ld16<R, E>(phi + checked((long long)wrap_dn(z0, g.nz) * planeE + off_y, E, cnt), below);
+        ld16<R, E>(phi + checked((long long)z0 * planeE + off_y, E, cnt), cur);
     }
 
     for (int z = z0; z < z1; ++z) {
         const long long pz = (long long)z * planeE;
         R halo[E], pv[E], cv[E], lft[NC], rgt[NC];
         if (active) {
-            ld16<R, E>(phi + (long long)wrap_up(z, g.nz) * planeE + off_y, above);
-            if (yh >= 0) ld16<R, E>(phi + pz + off_h, halo);
-            ldcg16<R, E>(pi + pz + off_y, pv);
-            if (MODE == 1) ldcg16<R, E>(reinterpret_cast<const R *>(comp) + pz + off_y, cv);
+            ld16<R, E>(phi + checked((long long)wrap_up(z, g.nz) * planeE + off_y, E, cnt), above);
+            if (yh >= 0) ld16<R, E>(phi + checked(pz + off_h, E, cnt), halo);
+            const long long oy = checked(pz + off_y, E, cnt);
+            ldcg16<R, E>(pi + oy, pv);
+            if (MODE == 1) ldcg16<R, E>(reinterpret_cast<const R *>(comp) + oy, cv);
             if (lane == 0) {
+                const long long ol = checked(pz + off_l, NC, cnt);
 #pragma unroll
-                for (int a = 0; a < NC; ++a) lft[a] = __ldg(phi + pz + off_l + a);
+                for (int a = 0; a < NC; ++a) lft[a] = __ldg(phi + ol + a);
             }
             if (!right_in_warp) {
+                const long long orr = checked(pz + off_r, NC, cnt);
 #pragma unroll
-                for (int a = 0; a < NC; ++a) rgt[a] = __ldg(phi + pz + off_r + a);
+                for (int a = 0; a < NC; ++a) rgt[a] = __ldg(phi + orr + a);
             }
         }
         const int buf = (z - z0) & 1;
@@ -200,9 +205,10 @@ __global__ void __launch_bounds__(32 * BY) k_stream(const R *__restrict__ phi, R
                     if (MODE == 1) cv[e] = cm[a];
                 }
             }
-            st16<R, E>(phi_out + pz + off_y, outv);
-            st16<R, E>(pi + pz + off_y, pv);
-            if (MODE == 1) st16<R, E>(reinterpret_cast<R *>(comp) + pz + off_y, cv);
+            const long long oy = checked(pz + off_y, E, cnt);
+            st16<R, E>(phi_out + oy, outv);
+            st16<R, E>(pi + oy, pv);
+            if (MODE == 1) st16<R, E>(reinterpret_cast<R *>(comp) + oy, cv);
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -261,6 +267,8 @@ int default_zchunk(const StepArgs &a, int by) {
 }
 
 }  // namespace
+
+cudaError_t bounds_violations_stream(unsigned long long *n, bool reset) { return bounds_violations_here(n, reset); }
 
 bool stream_supported(const StepArgs &a, int tile_y, int zchunk) {
     const int by = tile_y ? tile_y : kDefaultBY;

@@ -23,6 +23,7 @@
 //
 // pi and comp of halo columns are read by the neighbouring blocks too, so this kernel reads
 // phi, pi, comp from the front buffers and writes all three to the back buffers.
+#include "lf2_bounds.cuh"
 #include "lf2_internal.cuh"
 
 namespace lf2 {
@@ -340,6 +341,9 @@ __device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restric
     const int gx0 = wrap_any(x0 - TP + rx0, g.nx);
     const int gy = wrap_any(y0 - T + ry, g.ny);
     const long long planeE = (long long)g.nx * g.ny * NC;
+#ifdef LF2_DEBUG_BOUNDS
+    const long long total = planeE * g.nz;  // elements of every field buffer
+#endif
     const int colE = (gy * g.nx + gx0) * NC;  // offset within a plane (< 2^31 for every lattice run here)
     const bool out_col =
         rx0 >= TP && rx0 < TP + TX && x0 + rx0 - TP < g.nx && ry >= T && ry < T + TY && y0 + ry - T < g.ny;
@@ -363,7 +367,11 @@ __device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restric
     // plane index of the next load, advanced with a compare instead of a modulo
     int pl = wrap_any(z0 - T, g.nz);
     {
+#ifdef LF2_DEBUG_BOUNDS
+        const long long off = checked((long long)pl * planeE + colE, W, total);
+#else
         const long long off = (long long)pl * planeE + colE;
+#endif
         vload_g<R, W>(phi + off, st.pf_phi);
         vload_cg<R, W>(pi + off, st.pf_pi);
         if (MODE == 1) vload_cg<R, W>(reinterpret_cast<const R *>(comp) + off, st.pf_c);
@@ -371,18 +379,38 @@ __device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restric
     const int ibeg = z0 - T, iend = z1 + T;
     // output plane of stage T in iteration i is i - T; stores start at i = z0 + T
     long long out_off = (long long)(z0 - 2 * T - 1) * planeE + colE;  // advanced before each use
+#ifdef LF2_DEBUG_BOUNDS
+    // every shared access of this thread lies in [s_own - row_e, s_own + ps + 2 ps (T - 1) +
+    // row_e + W) of the 2 T ps elements the block holds
+    const long long s_lo = checked((long long)s_own - row_e, (long long)ps + 2LL * ps * (T - 1) + 2LL * row_e + W,
+                                   2LL * T * ps);
+    R *const base = sm + (s_lo + row_e);
+#else
     R *const base = sm + s_own;
+#endif
     // x-neighbours by warp shuffle when every region row is a whole group of lanes within one
     // warp and the block is whole warps
     const bool shfl_x = (32 % RXT == 0) && ((RXT * RY) % 32 == 0);
     for (int i = ibeg; i < iend; ++i) {
         pl = (pl + 1 == g.nz) ? 0 : pl + 1;
+#ifdef LF2_DEBUG_BOUNDS
+        const long long noff = checked((long long)pl * planeE + colE, W, total);
+#else
         const long long noff = (long long)pl * planeE + colE;
+#endif
         out_off += planeE;
         const int par = i & 1;
+#ifdef LF2_DEBUG_BOUNDS
+        const bool store = out_col && i - T >= z0;
+        const long long oo = store ? checked(out_off, W, total) : out_off;
+        tb_iteration<R, NC, MODE, T, CX>(st, base + par * ps, base + (par ^ 1) * ps, 2 * ps, row_e, k, i + 1 < iend,
+                                         phi + noff, pi + noff, comp + noff, store,
+                                         phi_out + oo, pi_out + oo, comp_out + oo, shfl_x);
+#else
         tb_iteration<R, NC, MODE, T, CX>(st, base + par * ps, base + (par ^ 1) * ps, 2 * ps, row_e, k, i + 1 < iend,
                                          phi + noff, pi + noff, comp + noff, out_col && i - T >= z0,
                                          phi_out + out_off, pi_out + out_off, comp_out + out_off, shfl_x);
+#endif
     }
 }
 

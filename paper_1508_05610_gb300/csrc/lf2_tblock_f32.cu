@@ -4,6 +4,8 @@
 
 namespace lf2 {
 
+cudaError_t bounds_violations_tblock_f32(unsigned long long *n, bool reset) { return bounds_violations_here(n, reset); }
+
 cudaError_t launch_tblock_f32(const TbArgs &a, const TbConfig &c, cudaStream_t s) {
     const Coef32 k = make_coef32(a.p, a.dt);
     switch (a.ncomp) {

@@ -4,6 +4,8 @@
 
 namespace lf2 {
 
+cudaError_t bounds_violations_tblock_f64(unsigned long long *n, bool reset) { return bounds_violations_here(n, reset); }
+
 cudaError_t launch_tblock_f64(const TbArgs &a, const TbConfig &c, cudaStream_t s) {
     const Coef64 k = make_coef64(a.p, a.dt);
     if (a.ncomp > 2) return cudaErrorNotSupported;  // FP64 fields of 3+ components run one-step kernels

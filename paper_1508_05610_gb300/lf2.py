@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "liblf2.so")
+DEBUG_LIB_PATH = os.path.join(_HERE, "lib", "liblf2_debug.so")  # built with index checks (--debug-bounds)
 
 LF2_OK, LF2_ERR_INVALID, LF2_ERR_UNSUPPORTED, LF2_ERR_NOMEM, LF2_ERR_CUDA, LF2_ERR_TIMEOUT, LF2_ERR_STATE = range(7)
 LF2_F64, LF2_F32_KAHAN, LF2_F32 = 0, 1, 2
@@ -81,6 +82,7 @@ SIGNATURES = {
     "lf2_energy_noalloc": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.POINTER(lf2_energy_t), _vp],
     "lf2_leapfrog_energy": [_vp, _vp, ctypes.POINTER(lf2_params), ctypes.c_int, _vp, _vp],
     "lf2_field_check": [_vp, _vp],
+    "lf2_debug_bounds": [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int],
     "lf2_field_compare": [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp],
     "lf2_ensemble_create": [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(lf2_params),
                             ctypes.POINTER(_vp)],
@@ -246,6 +248,13 @@ def lf2_field_check(f, stream=None):
     """Raises LF2Error (LF2_ERR_TIMEOUT) if a grid barrier of the last multi-step
     lf2_leapfrog_energy run on f gave up."""
     _call("lf2_field_check", f, _stream_ptr(stream))
+
+
+def lf2_debug_bounds(reset=False) -> int:
+    """Index violations counted by the debug library (LF2Error LF2_ERR_UNSUPPORTED otherwise)."""
+    n = ctypes.c_ulonglong(0)
+    _call("lf2_debug_bounds", ctypes.byref(n), 1 if reset else 0)
+    return int(n.value)
 
 
 def lf2_field_compare(f, ref_ptr, ref_prec, which=0, stream=None) -> dict:

@@ -167,6 +167,13 @@ def test_injected_launch_failure_is_reported_before_any_device_call(lib, monkeyp
         lib.lf2_lattice_destroy(lat)
 
 
+def test_release_library_has_no_index_checks(lib):
+    """The index checks exist only in the debug build; the release library says so."""
+    with pytest.raises(lib.LF2Error) as e:
+        lib.lf2_debug_bounds()
+    assert e.value.status == lib.LF2_ERR_UNSUPPORTED
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1508_05610_gb300")
     for dirpath, _, files in os.walk(pkg):
