@@ -272,12 +272,16 @@ def run_gpu(args):
     done = 0
     for prec in pairs:
         lf2.lf2_leapfrog_init(pairs[prec].fphi, pairs[prec].fpi, p, stream)
+    e0 = {prec: lf2.lf2_energy(pairs[prec].fphi, pairs[prec].fpi, p, stream)["total"] for prec in pairs}
+    drift = {prec: 0.0 for prec in pairs}
     for n in (10, 100):
         for prec in pairs:
             lf2.lf2_leapfrog_ex(pairs[prec].fphi, pairs[prec].fpi, p, n - done, stream=stream, **cfgs[prec])
         done = n
         e64 = lf2.lf2_energy(pairs["f64"].fphi, pairs["f64"].fpi, p, stream)
         e32 = lf2.lf2_energy(pairs["f32k"].fphi, pairs["f32k"].fpi, p, stream)
+        for prec, e in (("f64", e64), ("f32k", e32)):
+            drift[prec] = max(drift[prec], abs(e["total"] - e0[prec]) / abs(e0[prec]))
         # FP64 error norms on the device (lf2_field_compare) against the FP64 run's buffers
         cphi = lf2.lf2_field_compare(pairs["f32k"].fphi, pairs["f64"].front().data_ptr(), lf2.LF2_F64, 0, stream)
         cpi = lf2.lf2_field_compare(pairs["f32k"].fpi, pairs["f64"].pi_front().data_ptr(), lf2.LF2_F64, 0, stream)
@@ -361,13 +365,15 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian phi0)",
         "config": {"workload": WORKLOAD + ", FP64, one step per HBM pass (plain path)", "lattice": [N, N, N],
                    "ncomp": NCOMP, "sites": sites, "precision": "f64", "parallelism": f"replicas x{world}",
-                   "l2_policy": "state 805 MB > 129 MB L2; no flush needed"},
+                   "l2_policy": "state 805 MB > 129 MB L2; no flush needed",
+                   "seed": replica_seed(0), "seed_rule": "rank r uses seed + r"},
         "roofline": roof("f64", t64, "k_stream_f64_c2_256"),
         "kernel": "k_stream (one step per launch)",
         "fp32_kahan": {"value": round(gsu(t32), 3), "unit": UNIT, "ms_per_step": round(t32 / args.steps * 1e3, 5),
                        "roofline": roof("f32k", t32, traffic_key("f32k", cfgs["f32k"])),
                        "plan": cfgs["f32k"], "launches": launches["f32k"], "speedup_vs_fp64": round(t64 / t32, 3),
-                       "error_vs_fp64": err},
+                       "error_vs_fp64": err,
+                       "energy_drift_max_100_steps": {k: float(f"{v:.3e}") for k, v in drift.items()}},
         "e2e": {"value": round(aggregate_gsu(sites, world, args.steps, t_e2e), 3), "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": (state_bytes + 64) / args.steps,
                 "note": "upload phi,pi from pinned host + half-kick + K steps + energy + download, per step"},
