@@ -76,20 +76,20 @@ __global__ void __launch_bounds__(kThreads) k_site_f32(const float *__restrict__
         load_site<float, NC>(phi, s + (wrap_up(z, g.nz) - z) * plane, g.sites, zp);
 #pragma unroll
         for (int a = 0; a < NC; ++a) p[a] = pi[o + a];
-        if (MODE == 2) {
+        if constexpr (MODE == 2) {
             kick_f32<NC>(c, xm, xp, ym, yp, zm, zp, p, k);
 #pragma unroll
             for (int a = 0; a < NC; ++a) pi[o + a] = p[a];
-            continue;
-        }
+        } else {
 #pragma unroll
-        for (int a = 0; a < NC; ++a) cm[a] = (MODE == 1) ? comp[o + a] : 0.0f;
-        update_f32<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, out, k);
+            for (int a = 0; a < NC; ++a) cm[a] = (MODE == 1) ? comp[o + a] : 0.0f;
+            update_f32<NC, MODE == 1>(c, xm, xp, ym, yp, zm, zp, p, cm, out, k);
 #pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            pi[o + a] = p[a];
-            phi_out[o + a] = out[a];
-            if (MODE == 1) comp[o + a] = cm[a];
+            for (int a = 0; a < NC; ++a) {
+                pi[o + a] = p[a];
+                phi_out[o + a] = out[a];
+                if (MODE == 1) comp[o + a] = cm[a];
+            }
         }
     }
 }

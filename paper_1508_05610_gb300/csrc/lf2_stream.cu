@@ -22,12 +22,10 @@ struct Vec16;
 template <>
 struct Vec16<float> {
     using T = float4;
-    static constexpr int E = 4;
 };
 template <>
 struct Vec16<double> {
     using T = double2;
-    static constexpr int E = 2;
 };
 
 // NV consecutive 16-byte vectors (E = NV * 16 / sizeof(R) elements).
