@@ -312,6 +312,40 @@ def test_n_component_tblock_parity_with_oracle_and_integer_exact(lf2, ora, ncomp
     assert np.array_equal(phi, ophi) and np.array_equal(pi, opi)
 
 
+# ------------------------------------------------ symmetries of the evolution on the GPU
+@pytest.mark.parametrize("prec,cfg", [("f64", {}), ("f32k", {}),
+                                      ("f32k", dict(kernel=2)),  # streaming
+                                      ("f32k", dict(kernel=3, depth=4, cx=2, tile_x=8, tile_y=8)),
+                                      ("f64", dict(kernel=3, depth=2, cx=1, tile_x=8, tile_y=4))])
+def test_symmetries_translation_and_z2_bitwise_u1_to_rounding(lf2, prec, cfg):
+    """Translation by a lattice vector and phi -> -phi commute with the step exactly (every site
+    runs the same round-to-nearest arithmetic, and RN is odd), so the fields must match bit for
+    bit.  The U(1) quarter turn (phi_0, phi_1) -> (-phi_1, phi_0) changes the order in which
+    |phi|^2 is accumulated, so it holds to rounding only."""
+    shape = (24, 16, 12)
+    kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)
+    phi0 = inputs.gaussian_field(*shape, 2, sigma=0.5, seed=231)
+    pi0 = inputs.gaussian_field(*shape, 2, sigma=0.2, seed=232)
+    if cfg:
+        cfg = dict(cfg)
+        cfg["kernel"] = {2: lf2.LF2_KERNEL_STREAM, 3: lf2.LF2_KERNEL_TBLOCK}[cfg["kernel"]]
+
+    def run(phi, pi):
+        return run_gpu(lf2, phi, pi, 9, prec, kw, **cfg)
+    base = run(phi0, pi0)
+    shift = lambda a: np.roll(a, (5, 3, 7), axis=(0, 1, 2))  # (z, y, x)
+    t = run(shift(phi0), shift(pi0))
+    assert np.array_equal(t[0], shift(base[0])) and np.array_equal(t[1], shift(base[1]))
+    assert abs(t[2]["total"] - base[2]["total"]) <= 1e-12 * abs(base[2]["total"])
+    z = run(-phi0, -pi0)
+    assert np.array_equal(z[0], -base[0]) and np.array_equal(z[1], -base[1])
+    assert z[2]["total"] == base[2]["total"]
+    rot = lambda a: np.stack([-a[..., 1], a[..., 0]], axis=-1)
+    u = run(rot(phi0), rot(pi0))
+    tol = 1e-13 if prec == "f64" else 1e-5
+    assert relmax(u[0], rot(base[0])) <= tol and relmax(u[1], rot(base[1])) <= tol
+
+
 # ------------------------------------------------ the paper's field operation: derivative
 @pytest.mark.parametrize("prec,ncomp", [("f64", 1), ("f64", 3), ("f32", 2), ("f32k", 6)])
 @pytest.mark.parametrize("dim", [0, 1, 2])
