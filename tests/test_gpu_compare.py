@@ -54,6 +54,58 @@ def test_compare_matches_numpy(lf2, shape, ncomp, prec, ref_dtype):
     assert got["relmax"] == want[0] / want[1]
 
 
+def wide_range_f32(shape, seed):
+    """FP32 values over the whole finite range below 2^21: exponents -150..20 (subnormals
+    included), plus +0 and -0, returned as their exact FP64 images."""
+    rng = np.random.default_rng(seed)
+    v = np.ldexp(rng.standard_normal(shape), rng.integers(-150, 21, shape)).astype(np.float32)
+    v.flat[::17] = 0.0
+    v.flat[5::29] = -0.0
+    return v.astype(np.float64)
+
+
+@pytest.mark.parametrize("prec,ref_dtype", [("f32", np.float64), ("f32k", np.float64), ("f64", np.float32),
+                                            ("f32", np.float32)])
+def test_float_to_double_widening_is_exact(lf2, prec, ref_dtype):
+    """The FP32 values the comparison kernel reads are widened to FP64 exactly, over every
+    exponent (normal and subnormal) and both signed zeros: against the exact images the
+    difference is zero everywhere, and the maximum |ref| is the exact one."""
+    import torch
+    shape, ncomp = (40, 16, 9), 2
+    v = wide_range_f32(shape + (ncomp,), inputs.BASE_SEED + 95)
+    f32 = v.astype(np.float32)
+    assert np.count_nonzero((f32 != 0) & (np.abs(f32) < np.finfo(np.float32).tiny)) > 100
+    assert np.count_nonzero(np.signbit(f32) & (f32 == 0)) > 0
+    ref = torch.from_numpy(np.ascontiguousarray(v.astype(ref_dtype))).cuda()
+    ref_prec = lf2.LF2_F64 if ref_dtype == np.float64 else lf2.LF2_F32
+    with lf2.System(shape, ncomp, prec) as s:
+        s.upload(v, np.zeros_like(v))
+        stored, _ = s.download()
+        got = lf2.lf2_field_compare(s.phi, ref.data_ptr(), ref_prec)
+    assert np.array_equal(stored.ravel(), v.ravel())  # upload and download are exact
+    assert got["max_abs_diff"] == 0.0 and got["sum_sq_diff"] == 0.0
+    assert got["max_abs_ref"] == np.max(np.abs(v))
+    assert abs(got["sum_sq_ref"] - np.sum(v * v)) <= 1e-12 * np.sum(v * v)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_widening_of_infinities_and_nan(lf2, prec):
+    """FP32 infinities widen to FP64 infinities and a NaN to a NaN: against zeros the largest
+    difference is inf, then NaN once a NaN is stored."""
+    import torch
+    v = np.zeros((8, 8, 8, 1))
+    v.flat[100], v.flat[200] = np.inf, -np.inf
+    zeros = torch.zeros(512, dtype=torch.float32, device="cuda")
+    with lf2.System((8, 8, 8), 1, prec) as s:
+        s.upload(v, np.zeros_like(v))
+        inf = lf2.lf2_field_compare(s.phi, zeros.data_ptr(), lf2.LF2_F32)
+        v.flat[300] = np.nan
+        s.upload(v, np.zeros_like(v))
+        nan = lf2.lf2_field_compare(s.phi, zeros.data_ptr(), lf2.LF2_F32)
+    assert inf["max_abs_diff"] == np.inf and inf["sum_sq_diff"] == np.inf and inf["max_abs_ref"] == 0.0
+    assert np.isnan(nan["max_abs_diff"]) and np.isnan(nan["sum_sq_diff"])
+
+
 def test_compare_identical_is_zero_and_nan_propagates(lf2):
     import torch
     phi = inputs.gaussian_field(16, 8, 6, 2, sigma=0.3, seed=inputs.BASE_SEED + 93)

@@ -75,6 +75,40 @@ def test_fused_records_and_fields_bitwise_equal_separate_calls(lf2, shape, ncomp
     assert np.all(rec[:, 4 + ncomp: 4 + 6] == 0) and np.all(rec[:, 4 + 6 + ncomp:] == 0)
 
 
+@pytest.mark.parametrize("shape,ncomp,prec", [((40, 16, 9), 2, "f32k"), ((64, 24, 33), 3, "f32"),
+                                               ((96, 96, 96), 1, "f32k")])
+def test_energy_of_float_storage_equals_double_storage_of_the_same_values(lf2, shape, ncomp, prec):
+    """The FP64 energy of FP32 storage widens each stored value exactly: fields that hold the
+    same values (FP32 values over exponents -150..20, subnormals and signed zeros included)
+    in FP32 and in FP64 storage give bitwise the same record, from the stand-alone reduction
+    and from the fused step kernel's record of its input state."""
+    import torch
+    rng = np.random.default_rng(inputs.BASE_SEED + 73)
+
+    def values():
+        v = np.ldexp(rng.standard_normal(shape + (ncomp,)), rng.integers(-150, 21, shape + (ncomp,)))
+        v = v.astype(np.float32)
+        v.flat[::13] = 0.0
+        v.flat[3::31] = -0.0
+        return v.astype(np.float64)
+
+    phi0, pi0 = values(), values()
+    p = lf2.params(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.2)
+    fused = torch.zeros((1, 16), dtype=torch.float64, device="cuda")
+    with lf2.System(shape, ncomp, prec) as a, lf2.System(shape, ncomp, "f64") as b:
+        a.upload(phi0, pi0)
+        b.upload(phi0, pi0)
+        ea = lf2.lf2_energy(a.phi, a.pi, p, ncomp=ncomp)
+        eb = lf2.lf2_energy(b.phi, b.pi, p, ncomp=ncomp)
+        lf2.lf2_leapfrog_energy(a.phi, a.pi, p, 1, fused.data_ptr())
+        torch.cuda.synchronize()
+    assert all(np.array_equal(np.asarray(ea[key]), np.asarray(eb[key])) for key in ea)
+    rec = fused[0].cpu().numpy()
+    assert rec[3] == eb["total"] and rec[0] == eb["kinetic"] and rec[1] == eb["gradient"]
+    assert np.array_equal(rec[4:4 + ncomp], np.asarray(eb["sum"])[:ncomp])
+    assert np.isfinite(eb["total"]) and eb["total"] > 0
+
+
 def test_32cube_fused_energy_every_step_vs_oracle(lf2, ora):
     """The 32^3 real FP64 workload (dt = 0.1, lambda = eta = 1, sigma = 0.1, 100 steps) with
     the energy and checksums of every step from the fused kernel, against the oracle."""
