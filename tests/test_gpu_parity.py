@@ -346,6 +346,92 @@ def test_symmetries_translation_and_z2_bitwise_u1_to_rounding(lf2, prec, cfg):
     assert relmax(u[0], rot(base[0])) <= tol and relmax(u[1], rot(base[1])) <= tol
 
 
+KERNEL_IDS = {1: "LF2_KERNEL_SITE", 2: "LF2_KERNEL_STREAM", 3: "LF2_KERNEL_TBLOCK"}
+
+
+def kernel_cfg(lf2, cfg):
+    cfg = dict(cfg)
+    if "kernel" in cfg:
+        cfg["kernel"] = getattr(lf2, KERNEL_IDS[cfg["kernel"]])
+    return cfg
+
+
+HOMOGENEOUS_CFGS = [("f64", {}), ("f64", dict(kernel=1)), ("f64", dict(kernel=2)),
+                    ("f64", dict(kernel=3, depth=3, cx=1, tile_x=8, tile_y=4)),
+                    ("f32k", {}), ("f32k", dict(kernel=1)), ("f32k", dict(kernel=2)),
+                    ("f32k", dict(kernel=3, depth=4, cx=2, tile_x=12, tile_y=6)),
+                    ("f32", dict(kernel=3, depth=2, cx=1, tile_x=16, tile_y=8))]
+
+
+@pytest.mark.parametrize("prec,cfg", HOMOGENEOUS_CFGS)
+@pytest.mark.parametrize("ncomp", [1, 2])
+def test_homogeneous_field_stays_homogeneous_and_follows_the_oscillator(lf2, ora, prec, cfg, ncomp):
+    """A spatially constant field has a vanishing lattice Laplacian, and every site runs the same
+    arithmetic on the same values: after any number of steps all sites hold bitwise the same phi
+    and pi (an indexing slip at a tile, chunk or periodic edge would break this).  The common
+    value follows the single-site anharmonic oscillator, which the oracle runs on a 1^3 lattice."""
+    nx, ny, nz = 40, 12, 9
+    kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)
+    phi_site = np.array([0.7, -0.45][:ncomp])
+    pi_site = np.array([0.2, 0.3][:ncomp])
+    phi0 = np.broadcast_to(phi_site, (nz, ny, nx, ncomp)).copy()
+    pi0 = np.broadcast_to(pi_site, (nz, ny, nx, ncomp)).copy()
+    phi, pi, _ = run_gpu(lf2, phi0, pi0, 13, prec, kw, **kernel_cfg(lf2, cfg))
+    assert np.array_equal(phi, np.broadcast_to(phi[0, 0, 0], phi.shape))
+    assert np.array_equal(pi, np.broadcast_to(pi[0, 0, 0], pi.shape))
+    ophi, opi = ora.evolve(phi0[:1, :1, :1], pi0[:1, :1, :1], 13, half_kick=True, **kw)
+    tol = F64_TOL if prec == "f64" else 1e-5
+    assert relmax(phi[:1, :1, :1], ophi) <= tol and relmax(pi[:1, :1, :1], opi) <= tol
+
+
+@pytest.mark.parametrize("prec,cfg", [("f64", {}), ("f32k", {}), ("f32", dict(kernel=2)),
+                                      ("f64", dict(kernel=3, depth=2, cx=1, tile_x=8, tile_y=4)),
+                                      ("f32k", dict(kernel=3, depth=4, cx=2, tile_x=12, tile_y=6))])
+def test_fixed_points_zero_and_vacuum(lf2, prec, cfg):
+    """phi = pi = 0 is a fixed point of every kernel exactly.  So is the vacuum |phi| = eta = 1
+    with pi = 0 and m2 = 0 in FP32 storage, whose force is the difference form (every neighbour
+    difference and |phi|^2 - eta^2 are exact zeros).  The FP64 update folds -6 phi/dx^2 into the
+    site's own coefficient (dt F = a nb - (dl |phi|^2 + b0) phi), whose two rounded products
+    cancel only to rounding: there the vacuum holds to a few units of 1e-17 per step (an exact
+    simulation of the folded update gives pi = 8.3e-17 after the half kick and 11 steps)."""
+    nx, ny, nz = 40, 12, 9
+    kw = dict(dx=1.0, dt=0.05, lam=1.0, eta=1.0, m2=0.0)
+    zero = np.zeros((nz, ny, nx, 2))
+    phi, pi, e = run_gpu(lf2, zero, zero, 11, prec, kw, **kernel_cfg(lf2, cfg))
+    assert np.all(phi == 0) and np.all(pi == 0)
+    assert e["total"] == 0.25 * nx * ny * nz  # lambda/4 eta^4 per site, exact
+    vac = np.zeros((nz, ny, nx, 2))
+    vac[..., 0] = 1.0
+    phi, pi, e = run_gpu(lf2, vac, zero, 11, prec, kw, **kernel_cfg(lf2, cfg))
+    if prec == "f64":
+        assert np.max(np.abs(phi - vac)) <= 1e-15 and np.max(np.abs(pi)) <= 1e-15
+    else:
+        assert np.array_equal(phi, vac) and np.all(pi == 0)
+    # the energy's synchronising half kick is FP64 arithmetic in the folded form for every
+    # storage precision: its pi_n is a rounding residual of about 1e-17 per site
+    assert abs(e["total"]) <= 1e-25
+
+
+@pytest.mark.parametrize("prec,cfg", [("f64", {}), ("f32k", {}), ("f64", dict(kernel=2)),
+                                      ("f64", dict(kernel=3, depth=2, cx=1, tile_x=8, tile_y=4)),
+                                      ("f32k", dict(kernel=3, depth=4, cx=2, tile_x=8, tile_y=8))])
+@pytest.mark.parametrize("perm", [(1, 0, 2), (2, 1, 0)])
+def test_axis_permutation_commutes_with_the_step_to_rounding(lf2, prec, cfg, perm):
+    """Relabelling two axes maps the lattice and the 7-point stencil onto themselves but changes
+    the order in which the directions' terms are added: the evolved fields equal the relabelled
+    ones to rounding, not bit for bit."""
+    shape = (16, 24, 12)  # (nx, ny, nz); arrays are (z, y, x, comp)
+    kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)
+    phi0 = inputs.gaussian_field(*shape, 2, sigma=0.5, seed=241)
+    pi0 = inputs.gaussian_field(*shape, 2, sigma=0.2, seed=242)
+    relabel = lambda a: np.ascontiguousarray(np.transpose(a, perm + (3,)))
+    base = run_gpu(lf2, phi0, pi0, 9, prec, kw, **kernel_cfg(lf2, cfg))
+    swapped = run_gpu(lf2, relabel(phi0), relabel(pi0), 9, prec, kw, **kernel_cfg(lf2, cfg))
+    tol = 1e-13 if prec == "f64" else 1e-5
+    assert relmax(swapped[0], relabel(base[0])) <= tol and relmax(swapped[1], relabel(base[1])) <= tol
+    assert abs(swapped[2]["total"] - base[2]["total"]) <= tol * abs(base[2]["total"])
+
+
 # ------------------------------------------------ the paper's field operation: derivative
 @pytest.mark.parametrize("prec,ncomp", [("f64", 1), ("f64", 3), ("f32", 2), ("f32k", 6)])
 @pytest.mark.parametrize("dim", [0, 1, 2])
