@@ -169,8 +169,10 @@ lf2_status lf2_field_write(lf2_field f, int which, const char *path, void *strea
 
 /* Reads a snapshot written by lf2_field_write (or any file of that layout and element type)
  * into the current values (which = 0) or the compensation (which = 2).  The file size must
- * match the field exactly.  Reading values resets the compensation to zero; read the
- * compensation afterwards for an exact restart.  Synchronises `stream`. */
+ * match the field exactly (else LF2_ERR_INVALID before anything is copied).  Reading values
+ * resets the compensation to zero; read the compensation afterwards for an exact restart.
+ * A read error part-way (LF2_ERR_INVALID for a short read, LF2_ERR_CUDA for a copy) leaves
+ * the buffer partly overwritten.  Synchronises `stream`. */
 lf2_status lf2_field_read(lf2_field f, int which, const char *path, void *stream);
 
 /* The first-order symmetric difference along dimension dim (0 = x, 1 = y, 2 = z), the
