@@ -245,7 +245,8 @@ lf2_status lf2_energy_device(lf2_field phi, lf2_field pi, const lf2_params *p, d
  * grid barrier between steps; larger ones run one launch per step.  Results are the same bits
  * either way.  A barrier that does not complete within about a second (all blocks of a
  * cooperative launch are resident, so it always completes) ends the run and leaves NaN in the
- * records from that step on; lf2_field_check(phi) then returns LF2_ERR_TIMEOUT.  Enqueues on `stream` without waiting; after the first call on phi (which may
+ * records from the step before that barrier on (a step's record is finished during the next
+ * step); lf2_field_check(phi) then returns LF2_ERR_TIMEOUT.  Enqueues on `stream` without waiting; after the first call on phi (which may
  * allocate its back buffer and energy scratch, so make it outside a stream capture) calls
  * allocate nothing and can be captured into a CUDA graph.  Calls on one phi share its energy
  * scratch with lf2_energy and lf2_energy_device: order them on one stream.

@@ -146,7 +146,7 @@ lf2_status ensure_tblock(lf2_field phi, lf2_field pi, cudaStream_t s) {
 lf2_status ensure_energy_scratch(lf2_field f) {
     if (!f->energy_scratch) {
         void *d = nullptr;
-        LF2_CUDA(cudaMalloc(&d, sizeof(double) * kEnergyScratchDoubles), "cudaMalloc(energy scratch)");
+        LF2_CUDA(cudaMalloc(&d, sizeof(double) * kFieldScratchDoubles), "cudaMalloc(energy scratch)");
         // the finished-block counter must start at zero (each reduction leaves it at zero)
         const double zero = 0.0;
         cudaError_t e = cudaMemcpy((double *)d + kEnergyCounterOffset, &zero, sizeof zero, cudaMemcpyHostToDevice);

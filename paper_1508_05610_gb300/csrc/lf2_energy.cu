@@ -316,42 +316,64 @@ __global__ void __launch_bounds__(kEnergyThreads)
 // of arithmetic and about as much again in launch gaps and in the serial reduction.  One
 // cooperative launch runs all steps: the same grid, site order and per-site code as
 // k_step_energy for the site blocks, a grid barrier between steps, and one extra block, which
-// owns no sites, reducing step k's partial rows while the site blocks run step k+1 (the rows
-// alternate between two sets).  The fields and every record are bitwise those of one launch
-// per step.
+// owns no sites and reduces the partial rows.  The fields and every record are bitwise those
+// of one launch per step.
+//
+// The barrier is split in two halves.  A site block arrives as soon as its part of step k is
+// written (that is all the next step needs), then sums its energy accumulators into its
+// partial row of step k, then waits.  The block sums thus overlap the barrier instead of
+// preceding it.  A site block writes its row of step k before it arrives at barrier k+1, so
+// the reducing block sums the rows of step k once barrier k+1 has completed, while the site
+// blocks run step k+2, and one more barrier after the last step completes its rows.  The rows
+// rotate over three sets: a site block writes the set of step k+3 only after barrier k+2,
+// which the reducing block joins only after it has read the rows of step k.
 
-// Barrier slots (arrivals, generation, error) in the scratch's last partial row, which the
-// two row sets (at most kStepsMaxBlocks rows each) leave free.
-constexpr int kStepsMaxBlocks = (kEnergyBlocks - 1) / 2;
-constexpr size_t kBarrierOffset = (size_t)(kEnergyBlocks - 1) * kEnergySlots;
+// The row sets (at most kStepsMaxBlocks rows each) start at kStepsRowsOffset of a field's
+// scratch; the barrier slots (arrivals, generation, error) fill the row after them.
+constexpr int kRowSets = kEnergyStepsRowSets;
+constexpr int kStepsMaxBlocks = kEnergyStepsBlocks;
+constexpr size_t kBarrierOffset = (size_t)kStepsRowsOffset + (size_t)kRowSets * kStepsMaxBlocks * kEnergySlots;
+static_assert(kBarrierOffset + kEnergySlots == (size_t)kFieldScratchDoubles, "multi-step scratch layout");
 // A barrier waits at most about a second (2^24 polls of >= 64 ns); co-residency, which the
 // cooperative launch guarantees, keeps real waits to microseconds.
 constexpr unsigned kBarrierPolls = 1u << 24;
 
-// Grid barrier with a bounded wait (`polls` polls): false if the wait ran out here or in
-// another block.
-__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned polls_max) {
-    __shared__ int s_ok;
+// Arrival half of the grid barrier: once every thread of the block has made its writes,
+// thread 0 publishes them (fence) and counts the block in; the last block to arrive resets
+// the count and advances the generation.  Returns, in thread 0, the generation before the
+// arrival, which grid_wait compares against.
+__device__ __forceinline__ unsigned grid_arrive(unsigned *bar) {
     __syncthreads();
+    unsigned g = 0u;
     if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();  // this block's writes are visible device-wide before it arrives
+        g = *(volatile unsigned *)(bar + 1);
+        __threadfence();
         if (atomicAdd(bar, 1u) == gridDim.x - 1) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned polls = 0;
-            while (*gen == g) {
-                if (++polls > polls_max) {
-                    atomicExch(bar + 2, 1u);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        }
+    }
+    return g;
+}
+
+// Waiting half: returns true once the generation has moved past g (every block arrived),
+// false when the wait ran out after polls_max polls, here or in another block (error flag).
+// The generation can move by one at most while a block waits, since no barrier completes
+// without this block's next arrival.
+__device__ __forceinline__ bool grid_wait(unsigned *bar, unsigned g, unsigned polls_max) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = bar + 1;
+        unsigned polls = 0;
+        while (*gen == g) {
+            if (++polls > polls_max) {
+                atomicExch(bar + 2, 1u);
+                ok = 0;
+                break;
             }
+            __nanosleep(64);
         }
         __threadfence();
         if (*(volatile unsigned *)(bar + 2) != 0u) ok = 0;
@@ -361,41 +383,61 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned polls_max) {
     return s_ok != 0;
 }
 
-// A run cut short by a barrier that did not complete leaves NaN records from that step on.
+// A run cut short by a barrier that did not complete leaves NaN records from `from` on (the
+// record of a step is finished during the next step, so `from` is the step before that barrier).
 __device__ __forceinline__ void poison_records(double *records, int from, int nsteps) {
     if (blockIdx.x != gridDim.x - 1 || threadIdx.x != 0) return;
     for (int j = from; j < nsteps; ++j)
         for (int i = 0; i < kEnergySlots; ++i) records[(size_t)j * kEnergySlots + i] = __longlong_as_double(0x7ff8000000000000LL);
 }
 
+// The step loop shared by the FP64 and FP32 kernels.  site(src, dst, s, acc) performs the
+// fused step + energy of site s.
+template <int NC, typename R, typename Site>
+__device__ __forceinline__ void steps_energy_loop(R *phi_a, R *phi_b, Geom g, const CoefE &ke, int nsteps,
+                                                  double *__restrict__ scratch, double *__restrict__ records,
+                                                  unsigned polls, double (&sh)[kNs<NC>][kEnergyThreads], Site site) {
+    constexpr int NS = kNs<NC>;
+    unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
+    const int nsb = (int)gridDim.x - 1;  // site blocks; the last block reduces
+    const bool reducer = (int)blockIdx.x == nsb;
+    const long long stride = (long long)nsb * blockDim.x;
+    auto rows_of = [&](int step) {
+        return scratch + kStepsRowsOffset + (size_t)(step % kRowSets) * nsb * kEnergySlots;
+    };
+    for (int step = 0; step <= nsteps; ++step) {
+        double acc[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) acc[j] = 0.0;
+        if (!reducer && step < nsteps) {
+            const R *src = (step & 1) ? phi_b : phi_a;
+            R *dst = (step & 1) ? phi_a : phi_b;
+            for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
+                site(src, dst, s, acc);
+        }
+        const unsigned gen = grid_arrive(bar);  // step's fields published (the final pass: rows only)
+        if (!reducer && step < nsteps) {
+            block_sum<NS>(acc, sh);
+            if (threadIdx.x < NS) rows_of(step)[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+        }
+        if (!grid_wait(bar, gen, polls)) {
+            poison_records(records, step > 0 ? step - 1 : 0, nsteps);
+            return;
+        }
+        if (reducer && step > 0)
+            reduce_rows<NC>(rows_of(step - 1), nsb, sh, ke, records + (size_t)(step - 1) * kEnergySlots, nullptr);
+    }
+}
+
 template <int NC>
 __global__ void __launch_bounds__(kEnergyThreads)
     k_steps_energy_f64(double *phi_a, double *phi_b, double *__restrict__ pi, Geom g, Coef64 k, CoefE ke, int nsteps,
                        double *__restrict__ scratch, double *__restrict__ records, unsigned polls) {
-    constexpr int NS = kNs<NC>;
-    __shared__ double sh[NS][kEnergyThreads];
-    unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
-    const int nsb = (int)gridDim.x - 1;  // site blocks; the last block reduces
-    const long long stride = (long long)nsb * blockDim.x;
-    for (int step = 0; step < nsteps; ++step) {
-        const double *src = (step & 1) ? phi_b : phi_a;
-        double *dst = (step & 1) ? phi_a : phi_b;
-        double acc[NS];
-#pragma unroll
-        for (int j = 0; j < NS; ++j) acc[j] = 0.0;
-        double *rows = scratch + (size_t)(step & 1) * nsb * kEnergySlots;
-        if ((int)blockIdx.x < nsb) {
-            for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
-                site_step_energy_f64<NC, true>(src, dst, pi, s, g, k, ke, acc);
-            block_sum<NS>(acc, sh);
-            if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
-        }
-        if (!grid_sync(bar, polls)) {
-            poison_records(records, step, nsteps);
-            return;
-        }
-        if ((int)blockIdx.x == nsb) reduce_rows<NC>(rows, nsb, sh, ke, records + (size_t)step * kEnergySlots, nullptr);
-    }
+    __shared__ double sh[kNs<NC>][kEnergyThreads];
+    steps_energy_loop<NC>(phi_a, phi_b, g, ke, nsteps, scratch, records, polls, sh,
+                          [&](const double *src, double *dst, long long s, double (&acc)[kNs<NC>]) {
+                              site_step_energy_f64<NC, true>(src, dst, pi, s, g, k, ke, acc);
+                          });
 }
 
 template <int NC, bool KAHAN>
@@ -403,30 +445,11 @@ __global__ void __launch_bounds__(kEnergyThreads)
     k_steps_energy_f32(float *phi_a, float *phi_b, float *__restrict__ pi, float *__restrict__ comp, Geom g, Coef32 k,
                        CoefE ke, int nsteps, double *__restrict__ scratch, double *__restrict__ records,
                        unsigned polls) {
-    constexpr int NS = kNs<NC>;
-    __shared__ double sh[NS][kEnergyThreads];
-    unsigned *bar = reinterpret_cast<unsigned *>(scratch + kBarrierOffset);
-    const int nsb = (int)gridDim.x - 1;  // site blocks; the last block reduces
-    const long long stride = (long long)nsb * blockDim.x;
-    for (int step = 0; step < nsteps; ++step) {
-        const float *src = (step & 1) ? phi_b : phi_a;
-        float *dst = (step & 1) ? phi_a : phi_b;
-        double acc[NS];
-#pragma unroll
-        for (int j = 0; j < NS; ++j) acc[j] = 0.0;
-        double *rows = scratch + (size_t)(step & 1) * nsb * kEnergySlots;
-        if ((int)blockIdx.x < nsb) {
-            for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.sites; s += stride)
-                site_step_energy_f32<NC, KAHAN, true>(src, dst, pi, comp, s, g, k, ke, acc);
-            block_sum<NS>(acc, sh);
-            if (threadIdx.x < NS) rows[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
-        }
-        if (!grid_sync(bar, polls)) {
-            poison_records(records, step, nsteps);
-            return;
-        }
-        if ((int)blockIdx.x == nsb) reduce_rows<NC>(rows, nsb, sh, ke, records + (size_t)step * kEnergySlots, nullptr);
-    }
+    __shared__ double sh[kNs<NC>][kEnergyThreads];
+    steps_energy_loop<NC>(phi_a, phi_b, g, ke, nsteps, scratch, records, polls, sh,
+                          [&](const float *src, float *dst, long long s, double (&acc)[kNs<NC>]) {
+                              site_step_energy_f32<NC, KAHAN, true>(src, dst, pi, comp, s, g, k, ke, acc);
+                          });
 }
 
 // One block per 256 sites up to kEnergyBlocks: small lattices (a 32^3 run with an energy every

@@ -27,7 +27,7 @@ struct lf2_field_s {
     float *comp[2] = {nullptr, nullptr};  // Kahan compensation of phi (F32_KAHAN); comp[cfront] current
     bool own_comp[2] = {false, false};
     int cfront = 0;
-    double *energy_scratch = nullptr;  // kEnergyScratchDoubles: partial rows, record, counter (device)
+    double *energy_scratch = nullptr;  // kFieldScratchDoubles: partial rows, record, counter, multi-step rows (device)
     double *energy_host = nullptr;     // one pinned lf2_energy_t
     lf2_ensemble ensemble = nullptr;   // the ensemble this field is a member of, if any
 };

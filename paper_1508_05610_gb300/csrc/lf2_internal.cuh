@@ -38,6 +38,14 @@ constexpr int kEnergyRecordOffset = kEnergyBlocks * kEnergySlots;
 constexpr int kEnergyCounterOffset = kEnergyRecordOffset + kEnergySlots;
 constexpr int kEnergyScratchDoubles = kEnergyCounterOffset + 1;
 static_assert(3 + 2 * kMaxComp <= kEnergySlots, "energy slots");
+// The multi-step step + energy kernel keeps, after that layout, three rotating sets of up to
+// kEnergyStepsBlocks partial rows and one row of barrier words.  A field's scratch
+// (kFieldScratchDoubles doubles) holds both parts; lf2_energy_noalloc's fixed array only the
+// first, since it never runs that kernel.
+constexpr int kEnergyStepsBlocks = 2 * 152 - 1;  // two 256-thread blocks per SM, less the reducing block
+constexpr int kEnergyStepsRowSets = 3;
+constexpr int kStepsRowsOffset = (kEnergyScratchDoubles + kEnergySlots - 1) / kEnergySlots * kEnergySlots;
+constexpr int kFieldScratchDoubles = kStepsRowsOffset + (kEnergyStepsRowSets * kEnergyStepsBlocks + 1) * kEnergySlots;
 // Energy of (phi, pi) as an lf2_energy_t record: written to scratch + kEnergyRecordOffset and,
 // when `record` is not NULL, also to `record` (device).  One launch.
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
