@@ -538,15 +538,30 @@ __global__ void __launch_bounds__(kEnergyThreads) k_compare(const RA *__restrict
     __shared__ bool s_last;
     double acc[kCmp] = {0.0, 0.0, 0.0, 0.0};
     MagMax max_d, max_r;
+    // The thread's elements i, i + stride, i + 2 stride, ... are taken kBatch at a time: all their
+    // loads are issued before the first is used (the bound checks come first, so no load is
+    // speculative), and the sums still run in element order.
+    constexpr int kBatch = 4;
     const long long stride = (long long)gridDim.x * blockDim.x;
-#pragma unroll 4  // several elements' loads in flight per thread; the summation order is unchanged
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double r = widen(__ldg(ref + i));
-        const double d = __dsub_rn(widen(__ldg(a + i)), r);
-        max_d.add(d);
-        max_r.add(r);
-        acc[2] = __fma_rn(d, d, acc[2]);
-        acc[3] = __fma_rn(r, r, acc[3]);
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kBatch * stride) {
+        RA av[kBatch];
+        RB rv[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const long long i = i0 + u * stride;
+            av[u] = i < n ? __ldg(a + i) : RA(0);
+            rv[u] = i < n ? __ldg(ref + i) : RB(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (i0 + u * stride >= n) break;
+            const double r = widen(rv[u]);
+            const double d = __dsub_rn(widen(av[u]), r);
+            max_d.add(d);
+            max_r.add(r);
+            acc[2] = __fma_rn(d, d, acc[2]);
+            acc[3] = __fma_rn(r, r, acc[3]);
+        }
     }
     acc[0] = max_d.value();
     acc[1] = max_r.value();
