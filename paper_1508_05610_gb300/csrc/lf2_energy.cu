@@ -402,8 +402,13 @@ __device__ __forceinline__ void steps_energy_loop(R *phi_a, R *phi_b, Geom g, co
     const int nsb = (int)gridDim.x - 1;  // site blocks; the last block reduces
     const bool reducer = (int)blockIdx.x == nsb;
     const long long stride = (long long)nsb * blockDim.x;
-    auto rows_of = [&](int step) {
-        return scratch + kStepsRowsOffset + (size_t)(step % kRowSets) * nsb * kEnergySlots;
+    // rows [first, first + count) of the set of `step`, inside the row-set region (checked in
+    // the debug build against that region, so neither the reduction layout before it nor the
+    // barrier row after it can be hit)
+    auto rows_of = [&](int step, long long first, long long count) {
+        const long long rel = checked((long long)(step % kRowSets) * nsb * kEnergySlots + first * kEnergySlots,
+                                      count * kEnergySlots, (long long)kRowSets * kStepsMaxBlocks * kEnergySlots);
+        return scratch + kStepsRowsOffset + rel;
     };
     for (int step = 0; step <= nsteps; ++step) {
         double acc[NS];
@@ -418,14 +423,14 @@ __device__ __forceinline__ void steps_energy_loop(R *phi_a, R *phi_b, Geom g, co
         const unsigned gen = grid_arrive(bar);  // step's fields published (the final pass: rows only)
         if (!reducer && step < nsteps) {
             block_sum<NS>(acc, sh);
-            if (threadIdx.x < NS) rows_of(step)[(size_t)blockIdx.x * kEnergySlots + threadIdx.x] = sh[threadIdx.x][0];
+            if (threadIdx.x < NS) rows_of(step, blockIdx.x, 1)[threadIdx.x] = sh[threadIdx.x][0];
         }
         if (!grid_wait(bar, gen, polls)) {
             poison_records(records, step > 0 ? step - 1 : 0, nsteps);
             return;
         }
         if (reducer && step > 0)
-            reduce_rows<NC>(rows_of(step - 1), nsb, sh, ke, records + (size_t)(step - 1) * kEnergySlots, nullptr);
+            reduce_rows<NC>(rows_of(step - 1, 0, nsb), nsb, sh, ke, records + (size_t)(step - 1) * kEnergySlots, nullptr);
     }
 }
 
