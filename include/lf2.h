@@ -53,7 +53,8 @@ extern "C" {
 typedef enum {
     LF2_OK = 0,
     LF2_ERR_INVALID = 1,     /* bad argument: NULL pointer, size, mismatched fields ... */
-    LF2_ERR_UNSUPPORTED = 2, /* valid in the paper's model but not built: dim != 3, ncomp > 2 */
+    LF2_ERR_UNSUPPORTED = 2, /* valid in the paper's model but not built here (dim != 3, ncomp > 6),
+                              * or a kernel variant that cannot run this shape (lf2_leapfrog_ex) */
     LF2_ERR_NOMEM = 3,       /* a device or host allocation failed */
     LF2_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
     LF2_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (reported by lf2_field_check) */
@@ -62,8 +63,10 @@ typedef enum {
 
 typedef enum { LF2_F64 = 0, LF2_F32_KAHAN = 1, LF2_F32 = 2 } lf2_precision;
 
-/* Most components a field may have.  1 and 2 run on every kernel; 3 to 6 on the
- * one-thread-per-site kernel. */
+/* Most components a field may have.  1 and 2 run on every kernel.  3, 4 and 6 run on the
+ * one-thread-per-site and the one-step streaming kernels in every precision, and on the
+ * temporal-blocking kernel in FP32 storage (depth 2-4; 2 for 6 components).  5 runs on the
+ * one-thread-per-site kernel only. */
 #define LF2_MAX_COMP 6
 
 typedef struct lf2_lattice_s *lf2_lattice;
@@ -103,7 +106,7 @@ typedef struct {
     int tile_y; /* rows of the x-y tile (STREAM, TBLOCK); 0 = default */
     int zchunk; /* z-planes per block (STREAM, TBLOCK); 0 = default */
     int depth;  /* temporal-blocking depth, steps fused per pass: 2, 3, 4, 6 or 8 (TBLOCK); 0 = 4 */
-    int cx;     /* adjacent x-columns per thread, 1 or 2 (TBLOCK); 0 = default */
+    int cx;     /* adjacent x-columns per thread, 1, 2 or 4 (TBLOCK; 4 for real FP32 fields); 0 = default */
 } lf2_step_config;
 
 /* ---------------------------------------------------------------------- lattice */
@@ -201,11 +204,21 @@ lf2_status lf2_field_update_halo(lf2_field f, void *stream);
 /* -------------------------------------------------------------------- leapfrog */
 
 /* Start of the staggered leapfrog: pi <- pi - (dt/2) F(phi), turning pi_0 into pi_{-1/2}.
+ * The paper (Sec. 1, Sec. 5) evolves classical fields but prints no integrator; the scheme
+ * taken here is the staggered kick-drift leapfrog (velocity Verlet with its two half kicks of
+ * consecutive steps merged): pi lives at half steps, one force evaluation per step, and this
+ * half kick starts it.  The force F is the 7-point Laplacian of the Site neighbours x+i, x-i
+ * (Sec. 3.4) minus dV/dphi_a, the equation of motion of the Lagrangian
+ * 1/2 sum_a (d phi_a)^2 - V.
  * phi and pi must share the lattice, ncomp and precision.  Also allocates phi's back and
  * compensation buffers if missing (so that later lf2_leapfrog calls allocate nothing). */
 lf2_status lf2_leapfrog_init(lf2_field phi, lf2_field pi, const lf2_params *p, void *stream);
 
-/* nsteps >= 0 leapfrog steps.  On entry phi holds phi_n and pi holds pi_{n-1/2}; on return
+/* nsteps >= 0 leapfrog steps of the staggered kick-drift scheme above (kick
+ * pi_{n+1/2} = pi_{n-1/2} + dt F(phi_n), then drift phi_{n+1} = phi_n + dt pi_{n+1/2}, every
+ * site reading the old phi_n; LF2_F32_KAHAN compensates the drift's rounding with the per-site
+ * term c: y = dt pi - c, t = phi + y, c = (t - phi) - y, phi = t).
+ * On entry phi holds phi_n and pi holds pi_{n-1/2}; on return
  * phi holds phi_{n+nsteps} and pi holds pi_{n+nsteps-1/2}.  phi's front and back buffers swap
  * after each step (no copy).  Uses the tuned kernel of lf2_tune when one was chosen for this
  * shape, else the default one; results are bitwise identical whichever kernel runs.  The
@@ -220,7 +233,12 @@ lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int
                            const lf2_step_config *cfg, void *stream);
 
 /* Energy and checksums at integer step n from phi_n and pi_{n-1/2}: the synchronised momentum
- * pi_n = pi_{n-1/2} + (dt/2) F(phi_n) is formed on the fly.  Accumulates in FP64 for every
+ * pi_n = pi_{n-1/2} + (dt/2) F(phi_n) is formed on the fly (the staggered scheme keeps pi at
+ * half steps, so the energy of an integer step needs it).  The paper prints no energy; the one
+ * taken is E = dx^3 sum_x [1/2 sum_a pi_{a,n}^2 + 1/(2 dx^2) sum_a sum_i (phi_a(x+i) - phi_a(x))^2
+ * + V(phi(x))], with forward differences along the Site neighbours x+i (Sec. 3.4): the gradient
+ * energy whose variation is exactly the 7-point Laplacian of the force, so that E is the
+ * quantity the leapfrog conserves to O(dt^2).  Accumulates in FP64 for every
  * precision, with a fixed reduction order (bitwise reproducible).  Writes *out and
  * synchronises `stream`. */
 lf2_status lf2_energy(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream);
@@ -290,12 +308,14 @@ lf2_status lf2_debug_bounds(unsigned long long *violations, int reset);
  * first call for a field; this variant allocates nothing: no cudaMalloc, cudaFree, pinned-host
  * or library allocation.  Its scratch is one fixed array inside the library (608 x 16 + 17
  * doubles, 78 KB) that every GPU which loads the library holds until the process exits.  The
- * reduction uses at most 608 blocks whatever the lattice, so every lattice fits; if the scratch
- * needed ever exceeded the array, the call would return LF2_ERR_UNSUPPORTED with a message.  The first call on a device
- * looks up the array's device address (make it before any stream capture).  All calls share
- * the array: calls whose work overlaps on the GPU (different streams, or several host
- * threads) race and must be serialised by the caller.  Arguments, result and synchronisation
- * are those of lf2_energy; the result is copied into *out. */
+ * reduction uses at most 608 blocks whatever the lattice, so every lattice the library accepts
+ * fits (the library checks the array's layout when it is compiled); there is no size to
+ * reject.  The first call on a device looks up the array's device address (make it before any
+ * stream capture).  All calls share the array: calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race and must be serialised by the caller.  Each call
+ * first clears the array's finished-block counter on its stream, so an overlap spoils only the
+ * overlapping calls' results, not later ones.  Arguments, result and synchronisation are those
+ * of lf2_energy; the result is copied into *out. */
 lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, lf2_energy_t *out, void *stream);
 
 /* -------------------------------------------------------------------- ensembles */

@@ -625,15 +625,16 @@ lf2_status lf2_energy_noalloc(lf2_field phi, lf2_field pi, const lf2_params *p, 
     if (st == LF2_OK) st = check_params(p);
     if (st != LF2_OK) return st;
     if (!out) return fail(LF2_ERR_INVALID, "output pointer is NULL");
-    const long long needed = energy_scratch_needed(phi->lat->sites);
-    if (needed > kEnergyScratchDoubles)
-        return fail(LF2_ERR_UNSUPPORTED, "energy reduction needs %lld scratch doubles, the fixed array holds %d",
-                    needed, kEnergyScratchDoubles);
+    // The reduction grid is capped at kEnergyBlocks whatever the lattice, so its partial rows,
+    // record and counter always fit the fixed array (checked at compile time next to it).
     double *scratch = nullptr;
     LF2_CUDA(energy_noalloc_scratch(&scratch), "cudaGetSymbolAddress(energy scratch)");
     cudaStream_t s = (cudaStream_t)stream;
-    // The reduction writes every partial row and the record it reads back, and leaves the
-    // finished-block counter at zero (where the zero-initialised array starts it).
+    // The last block of a reduction returns the finished-block counter to zero.  An earlier
+    // call that overlapped another on the GPU (a documented race) could leave it non-zero, so
+    // it is cleared on this call's stream first: the damage of an overlap stays in that call.
+    LF2_CUDA(cudaMemsetAsync(scratch + kEnergyCounterOffset, 0, sizeof(unsigned int), s), "counter reset");
+    // The reduction writes every partial row it reads and the record read back below.
     LF2_CUDA(launch_energy(phi->val[phi->front], pi->val[pi->front], geom_of(phi->lat), phi->ncomp, phi->prec, *p,
                            scratch, nullptr, s),
              "energy launch");

@@ -692,10 +692,6 @@ cudaError_t launch_compare(const void *a, bool a_double, const void *ref, bool r
     return compare_ref<float>((const float *)a, ref, ref_double, n, nb, scratch, s);
 }
 
-long long energy_scratch_needed(long long sites) {
-    return (long long)energy_grid(sites) * kEnergySlots + kEnergySlots + 1;
-}
-
 cudaError_t launch_energy(const void *phi, const void *pi, const Geom &g, int ncomp, lf2_precision prec,
                           const lf2_params &p, double *scratch, double *record, cudaStream_t s) {
     const CoefE k = make_coefE(p);
@@ -724,9 +720,15 @@ cudaError_t launch_step_energy(const StepArgs &a, double *scratch, double *recor
 // framework owns the device allocator, or that must not make allocation calls at all.
 // lf2_energy allocates its scratch on first use; lf2_energy_noalloc uses this file-scope array
 // instead.  Every GPU that loads the library holds it until process exit.  Its size is fixed
-// because the reduction grid has at most kEnergyBlocks blocks whatever the lattice; static
-// device memory starts zeroed, so the finished-block counter starts at zero as required.
+// because the reduction grid has at most kEnergyBlocks blocks whatever the lattice: the
+// partial rows, the record and the finished-block counter of any reduction fit, as the
+// assertion below checks.  Static device memory starts zeroed; lf2_energy_noalloc also clears
+// the counter before each launch.
 static __device__ __align__(256) double g_energy_noalloc[kEnergyScratchDoubles];
+static_assert(kEnergyRecordOffset >= kEnergyBlocks * kEnergySlots &&
+                  kEnergyCounterOffset >= kEnergyRecordOffset + kEnergySlots &&
+                  kEnergyCounterOffset + 1 <= kEnergyScratchDoubles,
+              "the fixed scratch must hold kEnergyBlocks partial rows, the record and the counter");
 
 namespace {
 constexpr int kMaxDevices = 64;

@@ -28,10 +28,17 @@ cudaError_t launch_site_step(const StepArgs &a, cudaStream_t s);
 bool stream_supported(const StepArgs &a, int tile_y, int zchunk);
 cudaError_t launch_stream_step(const StepArgs &a, int tile_y, int zchunk, int nsteps_hint, cudaStream_t s);
 
+// Multiprocessors of the current device (queried once per device, then cached); grid sizes
+// and the temporal-blocking wave model are derived from it.
+int device_sm_count();
+
 // Energy reduction scratch (device, kEnergyScratchDoubles doubles): one partial row of
 // kEnergySlots per block, then the record row (an lf2_energy_t), then an unsigned counter of
 // finished blocks that must be zero before the first launch (every launch leaves it zero).
-constexpr int kEnergyBlocks = 152 * 4;
+// The reduction grid is capped at a fixed 608 blocks (four per SM of a 152-SM GB300) rather
+// than at a multiple of the queried SM count: the cap fixes the partial rows, and with them
+// the order of the FP64 sums, so a record is the same bits on every device.
+constexpr int kEnergyBlocks = 608;
 constexpr int kEnergyThreads = 256;
 constexpr int kEnergySlots = 16;
 constexpr int kEnergyRecordOffset = kEnergyBlocks * kEnergySlots;
@@ -42,7 +49,10 @@ static_assert(3 + 2 * kMaxComp <= kEnergySlots, "energy slots");
 // kEnergyStepsBlocks partial rows and one row of barrier words.  A field's scratch
 // (kFieldScratchDoubles doubles) holds both parts; lf2_energy_noalloc's fixed array only the
 // first, since it never runs that kernel.
-constexpr int kEnergyStepsBlocks = 2 * 152 - 1;  // two 256-thread blocks per SM, less the reducing block
+// At most 303 site blocks (two 256-thread blocks per SM of a 152-SM GB300, less the reducing
+// block): a size bound of the row sets; the launch itself checks co-residency on the device it
+// runs on and falls back to one launch per step where the grid does not fit.
+constexpr int kEnergyStepsBlocks = 303;
 constexpr int kEnergyStepsRowSets = 3;
 constexpr int kStepsRowsOffset = (kEnergyScratchDoubles + kEnergySlots - 1) / kEnergySlots * kEnergySlots;
 constexpr int kFieldScratchDoubles = kStepsRowsOffset + (kEnergyStepsRowSets * kEnergyStepsBlocks + 1) * kEnergySlots;
@@ -129,10 +139,8 @@ cudaError_t bounds_violations_tblock_f32k(unsigned long long *n, bool reset);
 cudaError_t bounds_violations_tblock_f32(unsigned long long *n, bool reset);
 cudaError_t bounds_violations_energy(unsigned long long *n, bool reset);
 
-// Fixed-size scratch of lf2_energy_noalloc (kEnergyScratchDoubles doubles, 78 KB), and the
-// doubles one reduction over `sites` sites uses (partial rows, record, counter).
+// Fixed-size scratch of lf2_energy_noalloc (kEnergyScratchDoubles doubles, 78 KB).
 cudaError_t energy_noalloc_scratch(double **out);
-long long energy_scratch_needed(long long sites);
 
 // Conversions between host-side doubles and storage precision.
 cudaError_t launch_convert_from_f64(const double *src, void *dst, long long n, lf2_precision prec, cudaStream_t s);

@@ -4,6 +4,7 @@
 // Each thread owns one site (x, y, z) of the row-major lattice and reads its six periodic
 // neighbours x+-i (the Site jumps of Sec. 3.4 with the torus wrap of Sec. 3.3.1 done by
 // index arithmetic instead of a stored halo).
+#include <atomic>
 #include <type_traits>
 
 #include "lf2_bounds.cuh"
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(kThreads) k_site_f32(const float *__restrict__
 
 int grid_for(long long sites) {
     long long b = (sites + kThreads - 1) / kThreads;
-    const long long cap = 152LL * 16;
+    const long long cap = 16LL * device_sm_count();
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
@@ -317,6 +318,21 @@ cudaError_t launch_convert_to_f64(const void *src, double *dst, long long n, lf2
     if (prec == LF2_F64) return cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     k_f32_to_f64<<<grid_for(n), kThreads, 0, s>>>((const float *)src, dst, n);
     return cudaGetLastError();
+}
+
+int device_sm_count() {
+    // one entry per device ordinal; concurrent first calls store the same value
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        return 152;
+    }
+    cache[dev].store(n, std::memory_order_relaxed);
+    return n;
 }
 
 }  // namespace lf2

@@ -21,7 +21,6 @@ using namespace lf2;
 namespace {
 
 constexpr int kBinThreads = 256;
-constexpr int kBinBlocks = 152 * 2;
 constexpr int kMaxBins = 1024;
 
 template <typename R>
@@ -101,6 +100,7 @@ extern "C" lf2_status lf2_power_spectrum(lf2_field f, int comp, int nbins, doubl
     cufftHandle plan = 0;
     bool have_plan = false;
     lf2_status st = LF2_OK;
+    const int kBinBlocks = 2 * device_sm_count();  // two histogram blocks per SM
     cudaError_t e = cudaMalloc(&real, (size_t)sites * rsz);
     if (e == cudaSuccess) e = cudaMalloc(&spec, (size_t)n * n * (n / 2 + 1) * csz);
     if (e == cudaSuccess) e = cudaMalloc(&partials, (size_t)kBinBlocks * 3 * nbins * sizeof(double));
@@ -118,7 +118,8 @@ extern "C" lf2_status lf2_power_spectrum(lf2_field f, int comp, int nbins, doubl
     const double inv_volume = 1.0 / ((double)n * n * n);
     const size_t smem = (size_t)3 * nbins * sizeof(double);
     for (int c = c0; c < c1 && st == LF2_OK; ++c) {
-        const int g = (int)((sites + 255) / 256 < 152 * 16 ? (sites + 255) / 256 : 152 * 16);
+        const long long cap = 16LL * device_sm_count();
+        const int g = (int)((sites + 255) / 256 < cap ? (sites + 255) / 256 : cap);
         if (dbl)
             k_extract<double><<<g, 256, 0, s>>>((const double *)f->val[f->front], (double *)real, sites, f->ncomp, c);
         else

@@ -45,15 +45,16 @@ bool tblock_supported(const TbArgs &a, TbConfig &c) {
     if (c.zchunk == 0) {
         // Split z into m chunks, m minimising (waves of blocks) x (iterations per block): a
         // chunk of zc planes costs zc + 2 depth iterations, and with one block per SM a launch
-        // takes ceil(blocks / 152) waves.  More chunks shrink the last, partly filled wave
+        // takes ceil(blocks / SMs) waves.  More chunks shrink the last, partly filled wave
         // but add the 2 depth halo planes per chunk.
         const long long tiles = (long long)((a.g.nx + c.tile_x - 1) / c.tile_x) * ((a.g.ny + c.tile_y - 1) / c.tile_y);
+        const long long sms = device_sm_count();
         long long best = -1;
         for (int m = 1; m <= 64; ++m) {
             const int zc = (a.g.nz + m - 1) / m;
             if (m > 1 && zc < 2 * c.depth) break;
             const long long blocks = tiles * ((a.g.nz + zc - 1) / zc);
-            const long long cost = ((blocks + 151) / 152) * (zc + 2 * c.depth);
+            const long long cost = ((blocks + sms - 1) / sms) * (zc + 2 * c.depth);
             if (best < 0 || cost < best) {
                 best = cost;
                 c.zchunk = zc;

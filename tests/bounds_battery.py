@@ -45,8 +45,11 @@ def main(lib_path, out_path):
                 lf2.lf2_leapfrog_ex(s.phi, s.pi, p, 7, **cfg)
                 phi, pi = s.download()
                 e = lf2.lf2_energy(s.phi, s.pi, p, ncomp=ncomp)
+                # the same reduction on the library's fixed scratch array
+                e_fixed = lf2.lf2_energy_noalloc(s.phi, s.pi, p, ncomp=ncomp)
             out[f"c{ci}_{j}_phi"], out[f"c{ci}_{j}_pi"] = phi, pi
             out[f"c{ci}_{j}_energy"] = np.array([e["total"]])
+            out[f"c{ci}_{j}_energy_noalloc"] = np.array([e_fixed["total"], e_fixed["kinetic"], e_fixed["gradient"]])
     # fused step + energy: one launch per step (larger lattice) and all steps in one launch
     for ci, (shape, ncomp, prec) in enumerate([((16, 16, 16), 1, "f64"), ((80, 64, 48), 2, "f32k")]):
         nx, ny, nz = shape
