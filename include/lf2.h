@@ -107,6 +107,10 @@ typedef struct {
     int zchunk; /* z-planes per block (STREAM, TBLOCK); 0 = default */
     int depth;  /* temporal-blocking depth, steps fused per pass: 2, 3, 4, 6 or 8 (TBLOCK); 0 = 4 */
     int cx;     /* adjacent x-columns per thread, 1, 2 or 4 (TBLOCK; 4 for real FP32 fields); 0 = default */
+    int cluster; /* TBLOCK, FP32 storage, 1 or 2 components: CTAs per tile, 2, 4 or 8, one thread-block
+                  * cluster that splits the tile's tile_y + 2 depth region rows into equal bands and
+                  * exchanges the bands' edge rows through distributed shared memory (Blackwell);
+                  * 0 or 1 = one CTA per tile */
 } lf2_step_config;
 
 /* ---------------------------------------------------------------------- lattice */

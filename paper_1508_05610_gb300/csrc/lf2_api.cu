@@ -478,11 +478,12 @@ lf2_status lf2_leapfrog_ex(lf2_field phi, lf2_field pi, const lf2_params *p, int
 
     int done = 0;
     if (kernel == LF2_KERNEL_TBLOCK) {
-        TbConfig c{cfg->depth, cfg->cx, cfg->tile_x, tile_y, zchunk};
+        TbConfig c{cfg->depth, cfg->cx, cfg->tile_x, tile_y, zchunk, cfg->cluster};
         TbArgs ta = tb_args(phi, pi, p);
         if (!tblock_supported(ta, c))
-            return fail(LF2_ERR_UNSUPPORTED, "temporal blocking config (depth %d, cx %d, tile %dx%d) does not fit",
-                        c.depth, c.cx, c.tile_x, c.tile_y);
+            return fail(LF2_ERR_UNSUPPORTED,
+                        "temporal blocking config (depth %d, cx %d, tile %dx%d, cluster %d) does not fit", c.depth,
+                        c.cx, c.tile_x, c.tile_y, c.cluster);
         for (; done + c.depth <= nsteps; done += c.depth) {
             ta = tb_args(phi, pi, p);
             cudaError_t e = launch_tblock(ta, c, s);

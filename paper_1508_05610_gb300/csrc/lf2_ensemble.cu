@@ -97,7 +97,8 @@ lf2_status build_items(lf2_ensemble e, const TbConfig &c) {
 
 // Checks that configuration c runs on every member (temporarily filling defaults).
 bool config_fits(lf2_ensemble e, TbConfig c) {
-    if (e->ncomp > 2) return false;  // ensemble passes are built for one and two components
+    // every member must fit the pass (temporal blocking of 3, 4 and 6 components is FP32 only,
+    // one column per thread, depth 2 to 4 -- 2 for 6 components -- as for a single lattice)
     for (int m = 0; m < e->n; ++m) {
         TbArgs a = tb_args(e->phi[m], e->pi[m], &e->params[m]);
         TbConfig cm = c;

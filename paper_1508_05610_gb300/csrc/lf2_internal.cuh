@@ -94,6 +94,7 @@ struct TbArgs {
 };
 struct TbConfig {
     int depth, cx, tile_x, tile_y, zchunk;
+    int cluster;  // CTAs per tile (a thread-block cluster of bands along y); 0 or 1: one CTA
 };
 // One member lattice of an ensemble pass (device table entry).  Buffer f ^ 1 is written
 // when buffer f = front ^ flip is read.
@@ -118,6 +119,10 @@ struct TbEnsembleLaunch {
     lf2_precision prec;
 };
 cudaError_t launch_tblock_ensemble(const TbEnsembleLaunch &e, cudaStream_t s);
+
+// Whether a clustered temporal-blocking kernel exists for this storage size, component count,
+// depth, columns per thread and cluster size (FP32 storage, 1 or 2 components).
+bool tblock_cluster_built(int esz, int ncomp, int depth, int cx, int cluster);
 
 // Shape/configuration check; fills defaults for zero fields of `c`.
 bool tblock_supported(const TbArgs &a, TbConfig &c);

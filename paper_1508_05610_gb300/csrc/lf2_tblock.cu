@@ -15,6 +15,11 @@ namespace {
 constexpr int kTbMaxThreads = 512;  // the kernels' launch bound
 }  // namespace
 
+bool tblock_cluster_built(int esz, int ncomp, int depth, int cx, int cluster) {
+    return esz == 4 && ncomp <= 2 && (depth == 3 || depth == 4) && (cx == 1 || cx == 2 || cx == 4) &&
+           cx * ncomp * esz <= 16 && (cluster == 2 || cluster == 4 || cluster == 8);
+}
+
 bool tblock_supported(const TbArgs &a, TbConfig &c) {
     const int esz = a.prec == LF2_F64 ? 8 : 4;
     if (a.ncomp > 2) {
@@ -37,8 +42,14 @@ bool tblock_supported(const TbArgs &a, TbConfig &c) {
     if (c.tile_y == 0) c.tile_y = 16;
     if (c.tile_x < c.cx || c.tile_x % c.cx || c.tile_y < 1) return false;
     if (a.g.nx % c.cx) return false;
+    if (c.cluster <= 1) c.cluster = 1;
+    if (c.cluster > 1 && !tblock_cluster_built(esz, a.ncomp, c.depth, c.cx, c.cluster)) return false;
     const int TP = ((c.depth + c.cx - 1) / c.cx) * c.cx;
-    const int RX = c.tile_x + 2 * TP, RY = c.tile_y + 2 * c.depth;
+    const int RX = c.tile_x + 2 * TP;
+    // region rows of one CTA: the whole region, or one of `cluster` equal bands of it
+    if ((c.tile_y + 2 * c.depth) % c.cluster) return false;
+    const int RY = (c.tile_y + 2 * c.depth) / c.cluster;
+    if (c.cluster > 1 && RY < 2) return false;
     if ((RX / c.cx) * RY > kTbMaxThreads) return false;
     const size_t smem = (size_t)2 * c.depth * (RY + 2) * RX * a.ncomp * esz;
     if (smem > 227 * 1024) return false;
@@ -53,7 +64,7 @@ bool tblock_supported(const TbArgs &a, TbConfig &c) {
         for (int m = 1; m <= 64; ++m) {
             const int zc = (a.g.nz + m - 1) / m;
             if (m > 1 && zc < 2 * c.depth) break;
-            const long long blocks = tiles * ((a.g.nz + zc - 1) / zc);
+            const long long blocks = tiles * c.cluster * ((a.g.nz + zc - 1) / zc);
             const long long cost = ((blocks + sms - 1) / sms) * (zc + 2 * c.depth);
             if (best < 0 || cost < best) {
                 best = cost;

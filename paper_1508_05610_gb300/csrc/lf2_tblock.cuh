@@ -112,6 +112,54 @@ __device__ __forceinline__ int wrap_any(int v, int n) {
     return w < 0 ? w + n : w;
 }
 
+// Thread-block clusters: the CTAs of a cluster stack along y and each keeps its band of the
+// cluster's region rows.  A band's first and last rows are the y-neighbours of the bands next
+// to it; after each level's plane is written, those rows are also stored into the neighbour
+// CTA's halo row (distributed shared memory), and one cluster-wide barrier per iteration orders
+// the stores before the reads of the next iteration, as __syncthreads does for one CTA.
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// Stores N elements at the address that `p` (this CTA's shared memory) has in CTA `rank` of
+// the cluster.
+template <typename R, int N>
+__device__ __forceinline__ void vstore_cluster(const R *p, unsigned rank, const R (&v)[N]) {
+    using C = VecChunk<R, N>;
+    unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
+    unsigned w[N * sizeof(R) / 4];
+    memcpy(w, v, sizeof w);
+#pragma unroll
+    for (int q = 0; q < C::COUNT; ++q) {
+        const unsigned d = ra + q * C::CH;
+        const unsigned *u = w + q * (C::CH / 4);
+        if constexpr (C::CH == 16)
+            asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(d), "r"(u[0]), "r"(u[1]), "r"(u[2]),
+                         "r"(u[3])
+                         : "memory");
+        else if constexpr (C::CH == 8)
+            asm volatile("st.shared::cluster.v2.b32 [%0], {%1, %2};\n" ::"r"(d), "r"(u[0]), "r"(u[1]) : "memory");
+        else
+            asm volatile("st.shared::cluster.b32 [%0], %1;\n" ::"r"(d), "r"(u[0]) : "memory");
+    }
+}
+// Own plane value v at `p`: also into the halo row of the band above (push & 1: this is the
+// band's first row; the neighbour's halo row is `band` rows below p) and of the band below
+// (push & 2: last row; `band` rows above p).
+template <typename R, int W, int CL>
+__device__ __forceinline__ void push_edges(const R *p, unsigned push, unsigned rank, int band, const R (&v)[W]) {
+    if constexpr (CL > 1) {
+        if (push & 1u) vstore_cluster<R, W>(p + band, rank - 1, v);
+        if (push & 2u) vstore_cluster<R, W>(p - band, rank + 1, v);
+    }
+}
+
 // Per-thread state of the wavefront, kept in registers across iterations.
 template <typename R, int T, int W>
 struct TbState {
@@ -124,12 +172,14 @@ struct TbState {
 // One z-iteration of the wavefront.  Level l of the plane written in this iteration lives at
 // cur + l * ps2, the one written in the previous iteration at prev + l * ps2 (both already
 // offset to this thread's own columns).
-template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+// CL > 1: the CTA is one band of a cluster (push, rank, band as for push_edges).
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT, int CL = 1>
 __device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__restrict__ cur, const R *__restrict__ prev,
                                              int ps2, int row_e, const CoefT &k, bool load_next,
                                              const R *__restrict__ nphi, const R *__restrict__ npi,
                                              const float *__restrict__ ncomp, bool store, R *__restrict__ ophi,
-                                             R *__restrict__ opi, float *__restrict__ ocomp, bool shfl_x) {
+                                             R *__restrict__ opi, float *__restrict__ ocomp, bool shfl_x,
+                                             unsigned push = 0, unsigned rank = 0, int band = 0) {
     constexpr int W = CX * NC;
     R in_phi[W], in_pi[W], in_c[W];
 #pragma unroll
@@ -162,6 +212,7 @@ __device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__re
         if (MODE == 1) st.cq[0][e] = in_c[e];
     }
     vstore_s<R, W>(cur, in_phi);
+    push_edges<R, W, CL>(cur, push, rank, band, in_phi);
 
 #pragma unroll
     for (int s = 1; s <= T; ++s) {
@@ -301,13 +352,17 @@ __device__ __forceinline__ void tb_iteration(TbState<R, T, CX * NC> &st, R *__re
                 st.lv[s][2][e] = out[e];
             }
             vstore_s<R, W>(cur + s * ps2, out);
+            push_edges<R, W, CL>(cur + s * ps2, push, rank, band, out);
         } else if (store) {
             vstore_g<R, W>(ophi, out);
             vstore_g<R, W>(opi, st.pq[T]);
             if (MODE == 1) vstore_g<R, W>(reinterpret_cast<R *>(ocomp), st.cq[T]);
         }
     }
-    __syncthreads();
+    if constexpr (CL > 1)
+        cluster_sync();
+    else
+        __syncthreads();
 }
 
 // MODE: 0 = FP32 plain drift, 1 = FP32 Kahan drift, 3 = FP64.
@@ -317,38 +372,43 @@ constexpr int tb_min_blocks() {
     return (T <= 4 && CX * NC * sizeof(R) <= 8) ? 2 : 1;
 }
 
-// One tile x z-chunk of a temporal-blocking pass: (bx, by) is the tile, bz the chunk.
-template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
+// One tile x z-chunk of a temporal-blocking pass: (bx, by) is the tile, bz the chunk.  With
+// CL > 1 the tile's region rows (TY + 2T) are split into CL bands of equal height, one per CTA
+// of a cluster, and `rank` is this CTA's band; CL = 1 is one CTA per tile.
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT, int CL = 1>
 __device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restrict__ phi_out, const R *__restrict__ pi,
                                          R *__restrict__ pi_out, const float *__restrict__ comp,
                                          float *__restrict__ comp_out, const Geom &g, const CoefT &k, int TX, int TY,
-                                         int zchunk, int bx, int by, int bz) {
+                                         int zchunk, int bx, int by, int bz, unsigned rank = 0) {
     constexpr int TP = ((T + CX - 1) / CX) * CX;  // x halo, rounded to whole thread groups
     constexpr int W = CX * NC;                     // elements per thread per plane
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
 
-    const int RX = TX + 2 * TP, RY = TY + 2 * T;
+    const int RX = TX + 2 * TP, RY = (TY + 2 * T) / CL;  // RY: this CTA's rows
     const int RXT = RX / CX;
-    const int ps = (RY + 2) * RX * NC;  // elements per shared plane (one padding row above and below)
+    const int ps = (RY + 2) * RX * NC;  // elements per shared plane (one halo row above and below)
     const int t = threadIdx.x;
     const int tx = t % RXT, ry = t / RXT;
+    const int ryg = (int)rank * RY + ry;  // row within the tile's region
     const int rx0 = tx * CX;
     const int x0 = bx * TX, y0 = by * TY;
     const int z0 = bz * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
 
     const int gx0 = wrap_any(x0 - TP + rx0, g.nx);
-    const int gy = wrap_any(y0 - T + ry, g.ny);
+    const int gy = wrap_any(y0 - T + ryg, g.ny);
     const long long planeE = (long long)g.nx * g.ny * NC;
 #ifdef LF2_DEBUG_BOUNDS
     const long long total = planeE * g.nz;  // elements of every field buffer
 #endif
     const int colE = (gy * g.nx + gx0) * NC;  // offset within a plane (< 2^31 for every lattice run here)
     const bool out_col =
-        rx0 >= TP && rx0 < TP + TX && x0 + rx0 - TP < g.nx && ry >= T && ry < T + TY && y0 + ry - T < g.ny;
+        rx0 >= TP && rx0 < TP + TX && x0 + rx0 - TP < g.nx && ryg >= T && ryg < T + TY && y0 + ryg - T < g.ny;
     const int s_own = ((ry + 1) * RX + rx0) * NC;
     const int row_e = RX * NC;
+    // edge rows of a band with a neighbouring band in the cluster
+    const unsigned push = CL > 1 ? ((ry == 0 && rank > 0) ? 1u : 0u) | ((ry == RY - 1 && rank + 1 < CL) ? 2u : 0u) : 0u;
 
     TbState<R, T, W> st;
 #pragma unroll
@@ -403,13 +463,15 @@ __device__ __forceinline__ void tb_block(const R *__restrict__ phi, R *__restric
 #ifdef LF2_DEBUG_BOUNDS
         const bool store = out_col && i - T >= z0;
         const long long oo = store ? checked(out_off, W, total) : out_off;
-        tb_iteration<R, NC, MODE, T, CX>(st, base + par * ps, base + (par ^ 1) * ps, 2 * ps, row_e, k, i + 1 < iend,
-                                         phi + noff, pi + noff, comp + noff, store,
-                                         phi_out + oo, pi_out + oo, comp_out + oo, shfl_x);
+        tb_iteration<R, NC, MODE, T, CX, CoefT, CL>(st, base + par * ps, base + (par ^ 1) * ps, 2 * ps, row_e, k,
+                                                    i + 1 < iend, phi + noff, pi + noff, comp + noff, store,
+                                                    phi_out + oo, pi_out + oo, comp_out + oo, shfl_x, push, rank,
+                                                    RY * row_e);
 #else
-        tb_iteration<R, NC, MODE, T, CX>(st, base + par * ps, base + (par ^ 1) * ps, 2 * ps, row_e, k, i + 1 < iend,
-                                         phi + noff, pi + noff, comp + noff, out_col && i - T >= z0,
-                                         phi_out + out_off, pi_out + out_off, comp_out + out_off, shfl_x);
+        tb_iteration<R, NC, MODE, T, CX, CoefT, CL>(st, base + par * ps, base + (par ^ 1) * ps, 2 * ps, row_e, k,
+                                                    i + 1 < iend, phi + noff, pi + noff, comp + noff,
+                                                    out_col && i - T >= z0, phi_out + out_off, pi_out + out_off,
+                                                    comp_out + out_off, shfl_x, push, rank, RY * row_e);
 #endif
     }
 }
@@ -421,6 +483,17 @@ __global__ void __launch_bounds__(kTbMaxThreads, (tb_min_blocks<R, NC, T, CX>())
              int zchunk) {
     tb_block<R, NC, MODE, T, CX, CoefT>(phi, phi_out, pi, pi_out, comp, comp_out, g, k, TX, TY, zchunk, blockIdx.x,
                                         blockIdx.y, blockIdx.z);
+}
+
+// The same pass with CL CTAs per tile, one cluster each (cluster dimensions (1, CL, 1)):
+// blockIdx.y / CL is the tile row and the cluster rank the band.
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT, int CL>
+__global__ void __launch_bounds__(kTbMaxThreads, 1)
+    k_tblock_cluster(const R *__restrict__ phi, R *__restrict__ phi_out, const R *__restrict__ pi,
+                     R *__restrict__ pi_out, const float *__restrict__ comp, float *__restrict__ comp_out, Geom g,
+                     CoefT k, int TX, int TY, int zchunk) {
+    tb_block<R, NC, MODE, T, CX, CoefT, CL>(phi, phi_out, pi, pi_out, comp, comp_out, g, k, TX, TY, zchunk, blockIdx.x,
+                                            blockIdx.y / CL, blockIdx.z, cluster_rank());
 }
 
 // Ensemble pass: one launch covers the tiles of every member lattice, items ordered longest
@@ -471,6 +544,62 @@ cudaError_t launch_t(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStr
     return cudaGetLastError();
 }
 
+// A clustered pass: tiles of tile_x x tile_y output sites, CL CTAs per tile (a cluster of
+// dimensions (1, CL, 1)), each with (tile_y + 2T) / CL region rows.
+template <typename R, int NC, int MODE, int T, int CX, typename CoefT, int CL>
+cudaError_t launch_cluster_t(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStream_t s) {
+    constexpr int TP = ((T + CX - 1) / CX) * CX;
+    const int RX = c.tile_x + 2 * TP, RY = (c.tile_y + 2 * T) / CL;
+    const int threads = (RX / CX) * RY;
+    const size_t smem = (size_t)2 * T * (RY + 2) * RX * NC * sizeof(R);
+    auto kern = k_tblock_cluster<R, NC, MODE, T, CX, CoefT, CL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && CL > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.g.nx + c.tile_x - 1) / c.tile_x, ((a.g.ny + c.tile_y - 1) / c.tile_y) * CL,
+                       (a.g.nz + c.zchunk - 1) / c.zchunk);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CL;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorNotSupported;
+    return cudaLaunchKernelEx(&cfg, kern, (const R *)a.phi, (R *)a.phi_out, (const R *)a.pi, (R *)a.pi_out, a.comp,
+                              a.comp_out, a.g, k, c.tile_x, c.tile_y, c.zchunk);
+}
+
+// The clustered kernels that are built: FP32 storage, 1 or 2 components, depth 3 or 4, one
+// vector of at most 16 bytes per thread and plane, 2, 4 or 8 CTAs per cluster.
+template <typename R, int NC, int MODE, typename CoefT>
+cudaError_t launch_cluster_prec(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStream_t s) {
+    if constexpr (NC <= 2 && sizeof(R) == 4) {
+        switch (c.cx * 1000 + c.depth * 100 + c.cluster) {
+#define LF2_TBC_CASE(CXV, TV, CLV)                                                                     \
+            case CXV * 1000 + TV * 100 + CLV:                                                          \
+                if constexpr (CXV * NC * sizeof(R) <= 16) return launch_cluster_t<R, NC, MODE, TV, CXV, CoefT, CLV>(a, c, k, s); \
+                return cudaErrorNotSupported;
+            LF2_TBC_CASE(1, 3, 2) LF2_TBC_CASE(1, 3, 4) LF2_TBC_CASE(1, 3, 8)
+            LF2_TBC_CASE(1, 4, 2) LF2_TBC_CASE(1, 4, 4) LF2_TBC_CASE(1, 4, 8)
+            LF2_TBC_CASE(2, 3, 2) LF2_TBC_CASE(2, 3, 4) LF2_TBC_CASE(2, 3, 8)
+            LF2_TBC_CASE(2, 4, 2) LF2_TBC_CASE(2, 4, 4) LF2_TBC_CASE(2, 4, 8)
+            LF2_TBC_CASE(4, 3, 2) LF2_TBC_CASE(4, 3, 4) LF2_TBC_CASE(4, 3, 8)
+            LF2_TBC_CASE(4, 4, 2) LF2_TBC_CASE(4, 4, 4) LF2_TBC_CASE(4, 4, 8)
+#undef LF2_TBC_CASE
+            default: return cudaErrorNotSupported;
+        }
+    }
+    return cudaErrorNotSupported;
+}
+
 template <typename R, int NC, int MODE, int T, int CX, typename CoefT>
 cudaError_t launch_ens_t(const TbEnsembleLaunch &e, cudaStream_t s) {
     constexpr int TP = ((T + CX - 1) / CX) * CX;
@@ -500,6 +629,7 @@ cudaError_t launch_ens_t(const TbEnsembleLaunch &e, cudaStream_t s) {
 // each precision's instantiations live in their own translation unit.
 template <typename R, int NC, int MODE, typename CoefT>
 cudaError_t launch_prec(const TbArgs &a, const TbConfig &c, const CoefT &k, cudaStream_t s) {
+    if (c.cluster > 1) return launch_cluster_prec<R, NC, MODE, CoefT>(a, c, k, s);
     if constexpr (NC >= 3) {
         // 3 to 6 components: one column per thread; the per-column state grows with NC, so
         // 6 components run at depth 2 only (within the 128 registers of a 512-thread block)
@@ -531,16 +661,32 @@ cudaError_t launch_prec(const TbArgs &a, const TbConfig &c, const CoefT &k, cuda
 
 template <typename R, int NC, int MODE, typename CoefT>
 cudaError_t launch_ens_prec(const TbEnsembleLaunch &e, cudaStream_t s) {
-    switch (e.c.cx * 16 + e.c.depth) {
-#define LF2_TB_CASE(CXV, TV)                                                                      \
-    case CXV * 16 + TV:                                                                           \
-        if constexpr (CXV * NC * sizeof(R) <= 16) return launch_ens_t<R, NC, MODE, TV, CXV, CoefT>(e, s); \
-        return cudaErrorNotSupported;
-        LF2_TB_CASE(1, 2) LF2_TB_CASE(1, 3) LF2_TB_CASE(1, 4) LF2_TB_CASE(1, 6) LF2_TB_CASE(1, 8)
-        LF2_TB_CASE(2, 2) LF2_TB_CASE(2, 3) LF2_TB_CASE(2, 4) LF2_TB_CASE(2, 6) LF2_TB_CASE(2, 8)
-        LF2_TB_CASE(4, 2) LF2_TB_CASE(4, 3) LF2_TB_CASE(4, 4) LF2_TB_CASE(4, 6) LF2_TB_CASE(4, 8)
+    if constexpr (NC >= 3) {
+        // 3 to 6 components: one column per thread, depth 2 to 4 (2 for 6 components), as for
+        // a single lattice
+        if (e.c.cx != 1) return cudaErrorNotSupported;
+        switch (e.c.depth) {
+            case 2: return launch_ens_t<R, NC, MODE, 2, 1, CoefT>(e, s);
+            case 3:
+                if constexpr (NC <= 4) return launch_ens_t<R, NC, MODE, 3, 1, CoefT>(e, s);
+                return cudaErrorNotSupported;
+            case 4:
+                if constexpr (NC <= 4) return launch_ens_t<R, NC, MODE, 4, 1, CoefT>(e, s);
+                return cudaErrorNotSupported;
+            default: return cudaErrorNotSupported;
+        }
+    } else {
+        switch (e.c.cx * 16 + e.c.depth) {
+#define LF2_TB_CASE(CXV, TV)                                                                          \
+            case CXV * 16 + TV:                                                                       \
+                if constexpr (CXV * NC * sizeof(R) <= 16) return launch_ens_t<R, NC, MODE, TV, CXV, CoefT>(e, s); \
+                return cudaErrorNotSupported;
+            LF2_TB_CASE(1, 2) LF2_TB_CASE(1, 3) LF2_TB_CASE(1, 4) LF2_TB_CASE(1, 6) LF2_TB_CASE(1, 8)
+            LF2_TB_CASE(2, 2) LF2_TB_CASE(2, 3) LF2_TB_CASE(2, 4) LF2_TB_CASE(2, 6) LF2_TB_CASE(2, 8)
+            LF2_TB_CASE(4, 2) LF2_TB_CASE(4, 3) LF2_TB_CASE(4, 4) LF2_TB_CASE(4, 6) LF2_TB_CASE(4, 8)
 #undef LF2_TB_CASE
-        default: return cudaErrorNotSupported;
+            default: return cudaErrorNotSupported;
+        }
     }
 }
 

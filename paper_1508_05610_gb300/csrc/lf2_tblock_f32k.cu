@@ -19,9 +19,14 @@ cudaError_t launch_tblock_f32k(const TbArgs &a, const TbConfig &c, cudaStream_t 
 }
 
 cudaError_t launch_tblock_ensemble_f32k(const TbEnsembleLaunch &e, cudaStream_t s) {
-    if (e.ncomp > 2) return cudaErrorNotSupported;  // ensembles of 3+ components run one-step kernels
-    return e.ncomp == 1 ? tb::launch_ens_prec<float, 1, 1, Coef32>(e, s)
-                        : tb::launch_ens_prec<float, 2, 1, Coef32>(e, s);
+    switch (e.ncomp) {
+        case 1: return tb::launch_ens_prec<float, 1, 1, Coef32>(e, s);
+        case 2: return tb::launch_ens_prec<float, 2, 1, Coef32>(e, s);
+        case 3: return tb::launch_ens_prec<float, 3, 1, Coef32>(e, s);
+        case 4: return tb::launch_ens_prec<float, 4, 1, Coef32>(e, s);
+        case 6: return tb::launch_ens_prec<float, 6, 1, Coef32>(e, s);
+        default: return cudaErrorNotSupported;
+    }
 }
 
 }  // namespace lf2

@@ -47,10 +47,16 @@ void read_file_locked() {
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int v[12];
-    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
-                  &v[8], &v[9], &v[10], &v[11]) == 12) {
-        g_plans[Key{v[0], v[1], v[2], v[3], v[4], v[5]}] = lf2_step_config{v[6], v[7], v[8], v[9], v[10], v[11]};
+    // one plan per line: the key's 6 integers, then kernel, tile_x, tile_y, zchunk, depth, cx,
+    // cluster
+    int v[13];
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        v[12] = 0;
+        const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
+                               &v[6], &v[7], &v[8], &v[9], &v[10], &v[11], &v[12]);
+        if (got < 12) continue;
+        g_plans[Key{v[0], v[1], v[2], v[3], v[4], v[5]}] = lf2_step_config{v[6], v[7], v[8], v[9], v[10], v[11], v[12]};
     }
     fclose(f);
 }
@@ -60,8 +66,9 @@ void append_file(const Key &k, const lf2_step_config &c) {
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
-            std::get<3>(k), std::get<4>(k), std::get<5>(k), c.kernel, c.tile_x, c.tile_y, c.zchunk, c.depth, c.cx);
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+            std::get<3>(k), std::get<4>(k), std::get<5>(k), c.kernel, c.tile_x, c.tile_y, c.zchunk, c.depth, c.cx,
+            c.cluster);
     fclose(f);
 }
 
@@ -86,6 +93,17 @@ std::vector<lf2_step_config> candidates(lf2_precision prec, int flags) {
             }
             out.push_back(lf2_step_config{LF2_KERNEL_TBLOCK, 32, 16, 0, depth, cx});
         }
+    }
+    if (!f64) {
+        // thread-block clusters: a warp per region row (32 threads x cx columns), 16 rows per
+        // CTA, 2 to 8 CTAs stacked along y; fewer halo rows per output row than one CTA holds
+        for (int depth : {3, 4})
+            for (int cx : {1, 2, 4})
+                for (int cl : {2, 4, 8}) {
+                    const int tp = ((depth + cx - 1) / cx) * cx;
+                    out.push_back(lf2_step_config{LF2_KERNEL_TBLOCK, 32 * cx - 2 * tp, 16 * cl - 2 * depth, 0, depth, cx,
+                                                  cl});
+                }
     }
     return out;
 }

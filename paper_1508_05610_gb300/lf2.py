@@ -41,7 +41,7 @@ class lf2_energy_t(ctypes.Structure):
 
 class lf2_step_config(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int),
-                ("depth", ctypes.c_int), ("cx", ctypes.c_int)]
+                ("depth", ctypes.c_int), ("cx", ctypes.c_int), ("cluster", ctypes.c_int)]
 
 
 class LF2Error(RuntimeError):
@@ -222,8 +222,8 @@ def lf2_leapfrog(phi, pi, p: lf2_params, nsteps, stream=None):
 
 
 def lf2_leapfrog_ex(phi, pi, p: lf2_params, nsteps, kernel=LF2_KERNEL_AUTO, tile_y=0, zchunk=0, depth=0,
-                    stream=None, tile_x=0, cx=0):
-    cfg = lf2_step_config(kernel, tile_x, tile_y, zchunk, depth, cx)
+                    stream=None, tile_x=0, cx=0, cluster=0):
+    cfg = lf2_step_config(kernel, tile_x, tile_y, zchunk, depth, cx, cluster)
     _call("lf2_leapfrog_ex", phi, pi, ctypes.byref(p), int(nsteps), ctypes.byref(cfg), _stream_ptr(stream))
 
 
@@ -284,7 +284,7 @@ LF2_TUNE_FORCE, LF2_TUNE_ONE_STEP = 1, 2
 
 def _cfg_dict(c):
     return {"kernel": c.kernel, "tile_x": c.tile_x, "tile_y": c.tile_y, "zchunk": c.zchunk, "depth": c.depth,
-            "cx": c.cx}
+            "cx": c.cx, "cluster": c.cluster}
 
 
 def lf2_tune(phi, pi, p: lf2_params, flags=0, stream=None) -> dict:

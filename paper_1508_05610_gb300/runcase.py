@@ -25,6 +25,7 @@ def main(argv=None):
     ap.add_argument("--cx", type=int, default=0)
     ap.add_argument("--tile", default="0x0", help="tile_x x tile_y (tile_y alone matters for stream)")
     ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--cluster", type=int, default=0, help="CTAs per tile (thread-block cluster), tblock only")
     ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--op", default="leapfrog",
@@ -116,7 +117,7 @@ def main(argv=None):
             cfg = {k: v for k, v in lf2.lf2_tune(fphi, fpi, p, stream=stream).items() if v}
         else:
             cfg = {"kernel": KERNELS[args.kernel], "depth": args.depth, "cx": args.cx, "tile_x": tx, "tile_y": ty,
-                   "zchunk": args.zchunk}
+                   "zchunk": args.zchunk, "cluster": args.cluster}
         lf2.lf2_leapfrog_ex(fphi, fpi, p, args.warmup, stream=stream, **cfg)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -27,9 +27,11 @@ def main(lib_path, out_path):
         # shape, ncomp, precision, kernel configurations
         ((40, 16, 9), 1, "f32k", [dict(kernel=lf2.LF2_KERNEL_SITE), dict(kernel=lf2.LF2_KERNEL_STREAM),
                                   dict(kernel=tb, depth=4, cx=2, tile_x=16, tile_y=8),
-                                  dict(kernel=tb, depth=3, cx=1, tile_x=12, tile_y=6, zchunk=4)]),
+                                  dict(kernel=tb, depth=3, cx=1, tile_x=12, tile_y=6, zchunk=4),
+                                  dict(kernel=tb, depth=4, cx=2, tile_x=24, tile_y=8, cluster=2)]),
         ((34, 8, 6), 2, "f64", [dict(kernel=lf2.LF2_KERNEL_STREAM), dict(kernel=tb, depth=2, cx=1, tile_x=8, tile_y=4)]),
-        ((32, 12, 7), 2, "f32", [dict(kernel=tb, depth=4, cx=2, tile_x=24, tile_y=8)]),
+        ((32, 12, 7), 2, "f32", [dict(kernel=tb, depth=4, cx=2, tile_x=24, tile_y=8),
+                                 dict(kernel=tb, depth=3, cx=2, tile_x=24, tile_y=10, cluster=4, zchunk=3)]),
         ((24, 12, 7), 4, "f32k", [dict(kernel=tb, depth=3, cx=1, tile_x=10, tile_y=8)]),
         ((33, 10, 6), 6, "f32", [dict(kernel=tb, depth=2, cx=1, tile_x=12, tile_y=8), dict(kernel=lf2.LF2_KERNEL_SITE)]),
         ((24, 8, 8), 3, "f64", [dict(kernel=lf2.LF2_KERNEL_STREAM)]),

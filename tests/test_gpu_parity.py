@@ -210,6 +210,67 @@ def test_tblock_bitwise_identical_to_single_steps(lf2, prec, shape, ncomp, pset)
     assert ran >= 20
 
 
+CLUSTER_SHAPES = [((64, 40, 12), 1), ((60, 36, 10), 2), ((128, 20, 9), 1), ((36, 70, 7), 2)]
+
+
+@pytest.mark.parametrize("prec", ["f32k", "f32"])
+@pytest.mark.parametrize("shape,ncomp", CLUSTER_SHAPES)
+def test_tblock_cluster_bitwise_identical_to_single_steps(lf2, prec, shape, ncomp):
+    """Temporal blocking with thread-block clusters (2, 4 or 8 CTAs per tile, each holding a band
+    of the tile's region rows and passing its edge rows to the neighbouring bands through
+    distributed shared memory): every depth, column width and cluster size, with ragged tiles,
+    bands of one to many warps and z-chunks, reproduces the one-step kernel bit for bit."""
+    nx, ny, nz = shape
+    kw = TB_PARAMS[0]
+    phi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.5, seed=27)
+    pi0 = inputs.gaussian_field(nx, ny, nz, ncomp, sigma=0.1, seed=28)
+    steps = 11
+    ref = run_gpu(lf2, phi0, pi0, steps, prec, kw, kernel=lf2.LF2_KERNEL_SITE)
+    ran = 0
+    for depth in (3, 4):
+        for cx in (1, 2, 4):
+            tp = -(-depth // cx) * cx
+            for cl in (2, 4, 8):
+                for band in (2, 16):
+                    tile_y = cl * band - 2 * depth
+                    for tile_x in (32 * cx - 2 * tp, 16 * cx - 2 * tp):
+                        if tile_y < 1 or tile_x < cx:
+                            continue
+                        for zchunk in (0, 4):
+                            try:
+                                got = run_gpu(lf2, phi0, pi0, steps, prec, kw, kernel=lf2.LF2_KERNEL_TBLOCK,
+                                              depth=depth, cx=cx, tile_x=tile_x, tile_y=tile_y, zchunk=zchunk,
+                                              cluster=cl)
+                            except lf2.LF2Error as e:
+                                assert e.status == lf2.LF2_ERR_UNSUPPORTED, e
+                                continue
+                            ran += 1
+                            cfg = (depth, cx, cl, tile_x, tile_y, zchunk)
+                            assert np.array_equal(got[0], ref[0]), cfg
+                            assert np.array_equal(got[1], ref[1]), cfg
+    assert ran >= 30
+
+
+def test_tblock_cluster_parity_with_oracle(lf2, ora):
+    """A clustered pass (depth 4, 4 CTAs per tile) on a ragged complex lattice: FP32 with the
+    compensated drift within a relative 1e-5 of the FP64 oracle after 10 steps, and integer data
+    (every operation exact) equal to the oracle bit for bit."""
+    nx, ny, nz = 72, 60, 11
+    kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)
+    phi0 = inputs.gaussian_field(nx, ny, nz, 2, sigma=0.5, seed=29)
+    pi0 = inputs.gaussian_field(nx, ny, nz, 2, sigma=0.1, seed=30)
+    ophi, opi = ora.evolve(phi0, pi0, 10, half_kick=True, **kw)
+    cfg = dict(kernel=lf2.LF2_KERNEL_TBLOCK, depth=4, cx=2, tile_x=56, tile_y=56, cluster=4)
+    phi, pi, _ = run_gpu(lf2, phi0, pi0, 10, "f32k", kw, **cfg)
+    assert relmax(phi, ophi) <= 1e-5 and relmax(pi, opi) <= 1e-5
+    ikw = dict(dx=1.0, dt=1.0, lam=0.0, eta=0.0, m2=0.0)
+    i0 = inputs.integer_field(nx, ny, nz, 2, lo=-4, hi=4, seed=31)
+    j0 = inputs.integer_field(nx, ny, nz, 2, lo=-4, hi=4, seed=32)
+    ophi, opi = ora.evolve(i0, j0, 4, **ikw)
+    phi, pi, _ = run_gpu(lf2, i0, j0, 4, "f32", ikw, half_kick=False, **cfg)
+    assert np.array_equal(phi, ophi) and np.array_equal(pi, opi)
+
+
 def test_tblock_fp64_parity_with_oracle(lf2, ora):
     nx, ny, nz = 48, 20, 13
     kw = dict(dx=0.9, dt=0.07, lam=1.3, eta=0.8, m2=0.05)

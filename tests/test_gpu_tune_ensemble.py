@@ -136,6 +136,44 @@ def test_ensemble_members_equal_standalone_runs(lf2, prec, ncomp):
             s.close()
 
 
+@pytest.mark.parametrize("prec,ncomp,depth", [("f32k", 3, 3), ("f32", 4, 4), ("f32k", 4, 2), ("f32k", 6, 2)])
+def test_ensemble_of_many_component_fields_runs_temporal_blocking(lf2, ora, prec, ncomp, depth):
+    """Ensembles of 3-, 4- and 6-component O(N) fields on temporal-blocking passes (one column
+    per thread): every member bitwise equal to the same lattice on the one-thread-per-site
+    kernel, and within a relative 1e-5 of the FP64 oracle, for 11 steps (whole passes plus
+    single steps) and again for 11 more (the other buffer parity)."""
+    systems, plist, starts = [], [], []
+    try:
+        for i, (shape, lam) in enumerate(ENSEMBLE):
+            kw = dict(dx=1.0, dt=0.05, lam=lam, eta=1.0, m2=0.0)
+            phi0 = inputs.gaussian_field(*shape, ncomp, sigma=0.3, seed=700 + i)
+            s = lf2.System(shape, ncomp, prec)
+            s.upload(phi0, np.zeros_like(phi0))
+            systems.append(s)
+            plist.append(lf2.params(**kw))
+            starts.append((phi0, kw))
+        e = lf2.lf2_ensemble_create([s.phi for s in systems], [s.pi for s in systems], plist)
+        try:
+            # raises LF2_ERR_UNSUPPORTED unless every member runs this temporal-blocking pass
+            lf2.lf2_ensemble_set_config(e, depth=depth, cx=1, tile_x=16 - 2 * depth, tile_y=8)
+            done = 0
+            for steps in (11, 11):
+                lf2.lf2_ensemble_run(e, steps)
+                done += steps
+                for s, (phi0, kw) in zip(systems, starts):
+                    got = s.download()
+                    ref = run_site(lf2, s.shape, ncomp, prec, phi0, np.zeros_like(phi0), kw, done)
+                    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), (s.shape, done)
+                    ophi, opi = ora.evolve(phi0, np.zeros_like(phi0), done, **kw)
+                    assert np.max(np.abs(got[0] - ophi)) <= 1e-5 * np.max(np.abs(ophi)), (s.shape, done)
+                    assert np.max(np.abs(got[1] - opi)) <= 1e-5 * np.max(np.abs(opi)), (s.shape, done)
+        finally:
+            lf2.lf2_ensemble_destroy(e)
+    finally:
+        for s in systems:
+            s.close()
+
+
 def test_ensemble_tune_and_configs_bitwise(lf2):
     prec, ncomp = "f32k", 1
     systems, refs, plist = [], [], []
